@@ -1,0 +1,567 @@
+#!/usr/bin/env python3
+"""Benchmark of the bandwidth-bound kernels on GB300: achieved HBM GB/s per
+kernel and for the whole sweep, against the measured copy roofline.
+
+One step = one pass of every kernel over the FP32 + FP64 size sweep:
+  vectors n = round(10^(3+k/3)), k = 0..15 (1e3 .. 1e8), U(-1, 1):
+      copy x <- y, update x <- y + 0.5 z, inner product <y, z>
+  dense GEMV y = A x, A ~ N(0, 1), 512^2 .. 16384^2, row- and column-major
+  CSR SpMV: 3D 7-point Laplacian 128^3 (6/-1) and power-law random CSR with
+      2,000,000 rows (row length 4..256, mean 16), values N(0, 1)
+Every buffer is read once per step and gigabytes of other traffic pass between
+two reads of the same buffer, so L2 (126 MB) holds nothing useful across
+reuses; the whole step moves ~25 GB.
+
+Bytes are algorithmic (minimum) bytes, the paper's convention (Sec. 3): for
+GEMV the right-hand side counts once; for SpMV x counts once.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the deliberately slow baseline)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HBM GB/s & % of peak per kernel; bf16/batched vs plain fp32 time at stated err"
+WORKLOAD = ("fp32+fp64 size sweep: vectors 1e3..1e8 (16 sizes; copy, x=y+0.5z, <y,z>), "
+            "GEMV row+col 512^2..16384^2, CSR SpMV 3D Laplacian 128^3 + power-law 2M rows")
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Max of a per-rank scalar (the timing rule: the slowest rank sets the time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons in the background."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the sweep workload
+# ---------------------------------------------------------------------------
+
+class Item:
+    """One kernel launch of the step: pre-marshalled C-ABI call plus its
+    algorithmic byte count."""
+    __slots__ = ("name", "op", "dtype", "size", "nbytes", "fn", "args", "h2d", "d2h")
+
+    def __init__(self, name, op, dtype, size, nbytes, fn, args, h2d=(), d2h=()):
+        self.name, self.op, self.dtype, self.size = name, op, dtype, size
+        self.nbytes, self.fn, self.args = nbytes, fn, args
+        self.h2d, self.d2h = h2d, d2h      # (host, device) tensor pairs for the e2e leg
+
+
+def _aligned_slices(total_elems_list, dtype, device, align_elems):
+    import torch
+    offs, cur = [], 0
+    for n in total_elems_list:
+        offs.append(cur)
+        cur += (n + align_elems - 1) // align_elems * align_elems
+    buf = torch.empty(max(cur, 1), dtype=dtype, device=device)
+    return buf, [buf[o:o + n] for o, n in zip(offs, total_elems_list)]
+
+
+def build_sweep(device, stream_handle):
+    """Allocate and fill the sweep's inputs and return the ordered launch list."""
+    import ctypes
+
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300 import _native
+
+    lib = _native.load()
+    items = []
+    sizes = synth.vector_sweep_sizes()
+    gsizes = synth.gemv_sweep_sizes()
+    keep = []                                   # keep tensors alive
+    for storage, es, seed0 in (("f32", 4, 100), ("f64", 8, 200)):
+        dt = synth.torch_dtype(storage)
+        code = _native.DTYPES[storage]
+        # vectors: one flat buffer per role, 256-byte aligned sub-vectors
+        ybuf, ys = _aligned_slices(sizes, dt, device, 64)
+        zbuf, zs = _aligned_slices(sizes, dt, device, 64)
+        xbuf, xs = _aligned_slices(sizes, dt, device, 64)
+        synth.device_uniform_(ybuf, seed0 + 1)
+        synth.device_uniform_(zbuf, seed0 + 2)
+        xbuf.zero_()
+        outs = torch.zeros(len(sizes), dtype=dt, device=device)
+        keep += [ybuf, zbuf, xbuf, outs]
+        for n, y, x in zip(sizes, ys, xs):
+            items.append(Item(f"copy_{storage}_{n}", "copy", storage, n, 2 * n * es,
+                              lib.vec_copy, (x.data_ptr(), y.data_ptr(), n, code, None,
+                                             stream_handle), h2d=(y,), d2h=(x,)))
+        for n, y, z, x in zip(sizes, ys, zs, xs):
+            items.append(Item(f"axpy_{storage}_{n}", "axpy", storage, n, 3 * n * es,
+                              lib.vec_axpy, (x.data_ptr(), y.data_ptr(), z.data_ptr(), 0.5, n,
+                                             code, None, stream_handle), h2d=(y, z), d2h=(x,)))
+        for k, (n, y, z) in enumerate(zip(sizes, ys, zs)):
+            wsb = lak.vec_dot_workspace(n, storage)
+            ws = torch.zeros(wsb, dtype=torch.uint8, device=device)
+            keep.append(ws)
+            items.append(Item(f"dot_{storage}_{n}", "dot", storage, n, 2 * n * es,
+                              lib.vec_dot, (outs[k:k + 1].data_ptr(), y.data_ptr(), z.data_ptr(),
+                                            n, code, ws.data_ptr(), wsb, None, stream_handle),
+                              h2d=(y, z), d2h=(outs[k:k + 1],)))
+        # dense GEMV, both layouts
+        for layout, lcode in (("row", 0), ("col", 1)):
+            for k, n in enumerate(gsizes):
+                A = torch.empty(n * n, dtype=dt, device=device)
+                synth.device_normal_(A, seed0 + 10 + k + (50 if layout == "col" else 0))
+                xg = torch.empty(n, dtype=dt, device=device)
+                synth.device_uniform_(xg, seed0 + 30 + k)
+                yg = torch.zeros(n, dtype=dt, device=device)
+                wsb = lak.dense_gemv_workspace(n, n, layout, storage)
+                ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=device)
+                keep += [A, xg, yg, ws]
+                nbytes = (n * n + 2 * n) * es
+                items.append(Item(f"gemv_{layout}_{storage}_{n}", f"gemv_{layout}", storage,
+                                  n, nbytes, lib.dense_gemv,
+                                  (yg.data_ptr(), A.data_ptr(), xg.data_ptr(), n, n, n, lcode,
+                                   code, ws.data_ptr(), ws.numel(), None, stream_handle),
+                                  h2d=(A, xg), d2h=(yg,)))
+        # CSR SpMV
+        for name, (rp, ci, v), ncols in (
+                ("lap3d_128", synth.laplacian_3d(128, storage), 128 ** 3),
+                ("powerlaw_2m", synth.powerlaw_csr(2_000_000, 2_000_000, 1, storage), 2_000_000)):
+            rpd, cid, vd = rp.to(device), ci.to(device), v.to(device)
+            xsp = torch.empty(ncols, dtype=dt, device=device)
+            synth.device_uniform_(xsp, seed0 + 40)
+            m = rp.numel() - 1
+            nnz = v.numel()
+            ysp = torch.zeros(m, dtype=dt, device=device)
+            keep += [rpd, cid, vd, xsp, ysp]
+            nbytes = nnz * (es + 4) + (m + 1) * 4 + ncols * es + m * es
+            items.append(Item(f"spmv_{name}_{storage}", "spmv", storage, m, nbytes, lib.csr_spmv,
+                              (ysp.data_ptr(), rpd.data_ptr(), cid.data_ptr(), vd.data_ptr(),
+                               xsp.data_ptr(), m, ncols, nnz, code, None, stream_handle),
+                              h2d=(rpd, cid, vd, xsp), d2h=(ysp,)))
+    return items, keep
+
+
+def run_step(items, lib_check, events=None):
+    for i, it in enumerate(items):
+        if events is not None:
+            events[i][0].record()
+        st = it.fn(*it.args)
+        if st != 0:
+            lib_check(it.name, st)
+        if events is not None:
+            events[i][1].record()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the reference arm and the cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def cpu_sample_items():
+    """A bounded sample of the sweep for the FP64 CPU oracle: every op and
+    dtype at a reduced size (vectors 1e6, GEMV 1024^2 both layouts, SpMV on the
+    3D Laplacian 32^3 and a 50,000-row power-law matrix)."""
+    import numpy as np
+
+    import synth
+    items = []
+    for storage, es in (("f32", 4), ("f64", 8)):
+        n = 1_000_000
+        y = synth.uniform(n, 1, storage).numpy()
+        z = synth.uniform(n, 2, storage).numpy()
+        items += [("copy", storage, 2 * n * es, ("copy", y)),
+                  ("axpy", storage, 3 * n * es, ("axpy", y, z)),
+                  ("dot", storage, 2 * n * es, ("dot", y, z))]
+        g = 1024
+        A = synth.normal((g, g), 3, storage).numpy().ravel()
+        xg = synth.uniform(g, 4, storage).numpy()
+        for lay in ("row", "col"):
+            items.append((f"gemv_{lay}", storage, (g * g + 2 * g) * es, ("gemv", A, xg, g, lay)))
+        for name, (rp, ci, v), nc in (("lap3d", synth.laplacian_3d(32, storage), 32 ** 3),
+                                      ("powerlaw", synth.powerlaw_csr(50_000, 50_000, 5, storage),
+                                       50_000)):
+            xs = synth.uniform(nc, 6, storage).numpy()
+            m = rp.numel() - 1
+            nnz = v.numel()
+            nbytes = nnz * (es + 4) + (m + 1) * 4 + nc * es + m * es
+            items.append((f"spmv_{name}", storage, nbytes,
+                          ("spmv", rp.numpy(), ci.numpy(), v.numpy(), xs)))
+    del np
+    return items
+
+
+def cpu_run(items):
+    import oracle
+    nbytes = 0
+    for _, _, b, call in items:
+        kind = call[0]
+        if kind == "copy":
+            oracle.copy(call[1])
+        elif kind == "axpy":
+            oracle.axpy(call[1], call[2], 0.5)
+        elif kind == "dot":
+            oracle.dot(call[1], call[2])
+        elif kind == "gemv":
+            _, A, x, g, lay = call
+            oracle.gemv(A, x, g, g, g, lay)
+        elif kind == "spmv":
+            oracle.csr_spmv(call[1], call[2], call[3], call[4])
+        nbytes += b
+    return nbytes
+
+
+CPU_SAMPLE_DESC = ("oracle (plain C, FP64 compensated sums, single thread) on a bounded sample: "
+                   "f32+f64 vectors n=1e6 (copy, update, dot), GEMV 1024^2 row+col, SpMV 3D "
+                   "Laplacian 32^3 + power-law 50k rows; GB/s from the same algorithmic bytes")
+
+
+def cpu_baseline(min_seconds: float = 10.0):
+    import oracle
+    oracle.build()
+    items = cpu_sample_items()
+    cpu_run(items)                               # warm caches / page in
+    t0 = time.perf_counter()
+    total, passes = 0, 0
+    while True:
+        total += cpu_run(items)
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": total / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_DESC}; {passes} passes in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    items = cpu_sample_items()
+    for _ in range(args.warmup):
+        cpu_run(items)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        total += cpu_run(items)
+    el = time.perf_counter() - t0
+    value = total / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 storage, f64 arithmetic", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_sample": CPU_SAMPLE_DESC},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": CPU_SAMPLE_DESC},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gb300(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+
+    import paper_1409_0669_gb300 as lak  # noqa: F401
+    from paper_1409_0669_gb300 import _native
+
+    stream = torch.cuda.Stream(device=device)
+    sh = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        items, keep = build_sweep(device, sh)
+    torch.cuda.synchronize()
+
+    def lib_check(name, st):
+        raise _native.LakError(name, st, _native.last_error())
+
+    bytes_per_step = sum(it.nbytes for it in items)
+    K, W = args.steps, args.warmup
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            run_step(items, lib_check)
+    torch.cuda.synchronize()
+
+    # per-launch events on the launching stream, all K steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in items] for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(dist, device)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        start.record()
+        for k in range(K):
+            run_step(items, lib_check, ev[k])
+        stop.record()
+    torch.cuda.synchronize()
+    barrier(dist, device)
+    time.sleep(0.2)
+    clocks = sampler.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, device)
+
+    per = {}
+    for i, it in enumerate(items):
+        t = sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)) / K
+        per[it.name] = (it, t)
+    kernel_ms_sum = sum(t for _, t in per.values())
+
+    ms_per_step = elapsed_ms / K
+    value = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+
+    # dominant kernel: largest share of the step's kernel time
+    dom_name, (dom_it, dom_ms) = max(per.items(), key=lambda kv: kv[1][1])
+    achieved = dom_it.nbytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom_name,
+                "share": dom_ms / kernel_ms_sum, "peak_source": f"{peak_kind} hbm_gbs"}
+    if args.traffic_json and os.path.exists(args.traffic_json):
+        with open(args.traffic_json) as fh:
+            roofline["traffic"] = json.load(fh).get(dom_name)
+
+    # per (op, dtype) summary at the largest size, and the paper's points
+    summary = {}
+    for name, (it, t) in per.items():
+        key = f"{it.op}_{it.dtype}"
+        gbs = it.nbytes / (t * 1e-3) / 1e9
+        if key not in summary or it.size >= summary[key]["size"]:
+            summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                            "us": round(t * 1e3, 2)}
+    for name in ("copy_f64_2154435", "axpy_f64_2154435", "dot_f64_2154435",
+                 "gemv_row_f64_2048"):
+        if name in per:
+            it, t = per[name]
+            summary["paper_point_" + name] = {"GBs": round(it.nbytes / (t * 1e-3) / 1e9, 1),
+                                              "us": round(t * 1e3, 2)}
+
+    if args.sweep_json:
+        rows = [{"name": n, "op": it.op, "dtype": it.dtype, "size": it.size, "bytes": it.nbytes,
+                 "us": t * 1e3, "GBs": it.nbytes / (t * 1e-3) / 1e9}
+                for n, (it, t) in per.items()]
+        with open(args.sweep_json, "w") as fh:
+            json.dump({"peak_gbs": peak, "rows": rows}, fh, indent=1)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = run_e2e(items, keep, stream, device, max(1, min(K, args.e2e_steps)), lib_check, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bytes_per_step": bytes_per_step,
+                   "launches_per_step": len(items),
+                   "l2": "inputs larger than L2: each buffer read once per step, >1 GB of other "
+                         "traffic between reuses (no explicit flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline, "per_kernel": summary, "e2e": e2e,
+        "gpu_launches": len(items) * K, "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    del keep
+    return 0
+
+
+def run_e2e(items, keep, stream, device, steps, lib_check, dist):
+    """The same step through the C ABI with inputs in pinned host memory: every
+    step copies each kernel's inputs host->device, runs it, and copies its
+    result device->host; the copies are inside the timed region."""
+    import torch
+    # one pinned host copy per distinct device input / output tensor
+    hmap = {}
+    for it in items:
+        for t in tuple(it.h2d) + tuple(it.d2h):
+            key = (t.data_ptr(), t.numel(), t.dtype)
+            if key not in hmap:
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t)
+                hmap[key] = h
+    h2d_bytes = d2h_bytes = 0
+    for it in items:
+        h2d_bytes += sum(t.numel() * t.element_size() for t in it.h2d)
+        d2h_bytes += sum(t.numel() * t.element_size() for t in it.d2h)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(dist, device)
+    with torch.cuda.stream(stream):
+        start.record()
+        for _ in range(steps):
+            for it in items:
+                for t in it.h2d:
+                    t.copy_(hmap[(t.data_ptr(), t.numel(), t.dtype)], non_blocking=True)
+                st = it.fn(*it.args)
+                if st != 0:
+                    lib_check(it.name, st)
+                for t in it.d2h:
+                    hmap[(t.data_ptr(), t.numel(), t.dtype)].copy_(t, non_blocking=True)
+        stop.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / steps
+    ms = max_over_ranks(ms, dist, device)
+    world = dist.get_world_size() if dist is not None else 1
+    nbytes = sum(it.nbytes for it in items)
+    hmap.clear()
+    return {"value": world * nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
+            "ms_per_step": ms, "steps": steps}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-json", default=None, help="write the per-size table here")
+    ap.add_argument("--traffic-json", default=None,
+                    help="per-kernel DRAM bytes per launch from an ncu capture")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

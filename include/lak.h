@@ -1,0 +1,215 @@
+/*
+ * lak.h -- C ABI of a GB300 (sm_103a) library of memory-bandwidth-bound
+ * linear-algebra kernels: the vector copy, vector update, inner product and
+ * dense matrix-vector product studied by Rupp, Tillet, Rudolf, Weinbub,
+ * Grasser and Juengel, "Performance Portability Study of Linear Algebra
+ * Kernels in OpenCL" (IWOCL'14), plus the CSR sparse matrix-vector product,
+ * all run under one shared launch-size configuration (lak_cfg).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Every array argument is DEVICE memory owned by the caller (for
+ *   instance a PyTorch CUDA tensor's data pointer) on the current CUDA device.
+ *   The library allocates nothing and frees nothing; where a kernel needs
+ *   scratch memory the caller passes it in ("workspace"), sized by the matching
+ *   *_workspace() query for the same arguments.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  Every call is asynchronous on that stream: no call
+ *   synchronises the host, and scalar results (vec_dot) stay on the device.
+ * Storage types (lak_dtype).  LAK_F32 and LAK_F64 compute in their own
+ *   precision; LAK_BF16 and LAK_F16 are reduced-precision STORAGE with FP32
+ *   arithmetic.  Results are rounded to the storage type with
+ *   round-to-nearest-even.
+ * Alignment.  Any element-aligned pointer is accepted.  Wide (up to 32-byte)
+ *   vector loads are used when the pointers of one call share their offset
+ *   modulo the load width; otherwise the call runs the same kernel with
+ *   one-element accesses.  Misalignment is never an error.
+ * Errors.  Arguments are checked on the host before anything is launched; a
+ *   failed check returns a negative lak_status and launches nothing.  A
+ *   launch that CUDA rejects returns LAK_ECUDA.  lak_last_error() gives a
+ *   human-readable message for the calling thread's last failure.  The
+ *   library never calls exit/abort and never traps on the device.
+ * Sizes.  Element counts and leading dimensions are int64_t; all device
+ *   index arithmetic is 64-bit.  CSR index arrays are int32 (nnz < 2^31).
+ * Aliasing.  vec_axpy allows x == y or x == z (in place); vec_dot allows
+ *   x == y.  Outputs of dense_gemv and csr_spmv must not overlap any input.
+ */
+#ifndef LAK_H
+#define LAK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LAK_API __attribute__((visibility("default")))
+#else
+#define LAK_API
+#endif
+
+typedef enum {
+    LAK_OK = 0,
+    LAK_EINVAL = -1,      /* bad size, pointer, leading dimension or config */
+    LAK_EDTYPE = -2,      /* unknown or unsupported storage type */
+    LAK_ELAYOUT = -3,     /* unknown matrix layout */
+    LAK_ECUDA = -4,       /* the CUDA runtime rejected a launch or query */
+    LAK_EWORKSPACE = -5   /* workspace missing or smaller than the query said */
+} lak_status;
+
+typedef enum { LAK_F32 = 0, LAK_F64 = 1, LAK_BF16 = 2, LAK_F16 = 3 } lak_dtype;
+
+typedef enum { LAK_ROW_MAJOR = 0, LAK_COL_MAJOR = 1 } lak_layout;
+
+/* Loop skeletons of Sec. 2: the index advances by the whole grid ("global
+ * increment") or each block walks one contiguous range ("local increment"). */
+typedef enum { LAK_INC_GLOBAL = 0, LAK_INC_LOCAL = 1 } lak_increment;
+
+typedef enum {
+    LAK_OP_COPY = 0, LAK_OP_AXPY = 1, LAK_OP_DOT = 2,
+    LAK_OP_GEMV_ROW = 3, LAK_OP_GEMV_COL = 4, LAK_OP_SPMV = 5,
+    LAK_OP_COUNT = 6
+} lak_op;
+
+/*
+ * Kernel configuration (Sec. 1 defines a configuration as source variant +
+ * local work size + global work size; Sec. 2 parameterises it by increment
+ * type, vector length, local size and number of work-groups).
+ *   block      threads per block, a multiple of 32 in [32, 512]    (0 = auto;
+ *              512 is also the largest local size the paper studies)
+ *   grid       number of blocks, >= 1                              (0 = auto)
+ *   vec        elements per thread per access group: 1, 2, 4, 8 or 16
+ *              (0 = auto).  Per op: copy/axpy/dot and row-major GEMV read
+ *              `vec` consecutive elements per thread per step; column-major
+ *              GEMV gives each thread `vec` consecutive rows; CSR SpMV issues
+ *              `vec` independent nonzero loads per thread per step.
+ *   increment  LAK_INC_GLOBAL or LAK_INC_LOCAL (ignored when block = 0)
+ * A NULL cfg, or one whose block is 0, takes the library default for the op
+ * and storage type (set by lak_set_default_cfg, e.g. from an autotuning
+ * cache, else built in); a zero grid or vec in an otherwise explicit cfg is
+ * filled in by the library.
+ */
+typedef struct {
+    int32_t block;
+    int32_t grid;
+    int32_t vec;
+    int32_t increment;
+} lak_cfg;
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+LAK_API const char *lak_last_error(void);
+
+/* ABI version of this header (bumped on any incompatible change). */
+LAK_API int32_t lak_abi_version(void);
+
+/*
+ * Replace the default configuration used for (op, dtype) when a call passes
+ * no explicit cfg; cfg = NULL restores the built-in default.  Process-wide;
+ * not synchronised against concurrent calls that read it.
+ */
+LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg);
+
+/*
+ * The configuration a call of `op` would launch with on the current device,
+ * after defaults and automatic fields are filled in.  Sizes: for the vector
+ * ops m = n = the vector length; for dense_gemv the matrix is m-by-n; for
+ * csr_spmv m rows, n columns and nnz stored entries (nnz is ignored by the
+ * other ops).  `vec` in *out is the vector width the call would actually use
+ * for aligned pointers.  Writes *out; returns LAK_OK or a negative status.
+ */
+LAK_API lak_status lak_resolve_cfg(lak_op op, lak_dtype dtype, int64_t m, int64_t n,
+                                   int64_t nnz, const lak_cfg *cfg, lak_cfg *out);
+
+/*
+ * vec_copy: x[i] = y[i] for 0 <= i < n  (Sec. 2, the copy operation x <- y,
+ * which the paper uses as the archetype whose good configurations carry over
+ * to the other operations, Sec. 3.2 and Sec. 4).  A bit copy of n elements of
+ * `dtype`; x and y must not overlap unless x == y.  n = 0 is a no-op.
+ */
+LAK_API lak_status vec_copy(void *x, const void *y, int64_t n, lak_dtype dtype,
+                            const lak_cfg *cfg, void *stream);
+
+/*
+ * vec_axpy: x[i] = y[i] + alpha * z[i] for 0 <= i < n  (Sec. 2's scaled
+ * vector addition x <- alpha*y + beta*z, taken with the first coefficient 1).
+ * alpha is rounded to the arithmetic type (FP32 for F32/BF16/F16 storage, FP64
+ * for F64) and each element is one fused multiply-add rounded once to the
+ * storage type.  x may equal y or z.  n = 0 is a no-op.
+ */
+LAK_API lak_status vec_axpy(void *x, const void *y, const void *z, double alpha,
+                            int64_t n, lak_dtype dtype, const lak_cfg *cfg,
+                            void *stream);
+
+/*
+ * Workspace bytes vec_dot needs for these arguments on the current device
+ * (a partial sum per block and one arrival counter).  0 on invalid input.
+ */
+LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg);
+
+/*
+ * vec_dot: *out = sum_i x[i] * y[i]  (Sec. 2's inner product, reduced in
+ * on-chip memory per work-group; the paper leaves the cross-group combine
+ * open).  Single pass: each thread accumulates in the arithmetic type, warps
+ * reduce with shuffles, each block's partial is combined in FP64 and written
+ * to the workspace, and the last block to arrive adds the partials in FP64 in
+ * block order, so the result is deterministic for a fixed configuration.
+ * `out` is one device element: float for F32/BF16/F16, double for F64.
+ * `workspace` (>= vec_dot_workspace() bytes, 8-byte aligned) must be
+ * zero-filled before its first use; every completed call leaves its counter at
+ * zero again, so it can be reused by later calls on the same stream.  Calls
+ * sharing a workspace must not overlap on the device.  n = 0 writes 0.
+ */
+LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
+                           lak_dtype dtype, void *workspace, size_t ws_bytes,
+                           const lak_cfg *cfg, void *stream);
+
+/*
+ * Workspace bytes dense_gemv needs (column-major split-K partials and per-tile
+ * counters; 0 for row-major) on the current device.
+ */
+LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout,
+                                    lak_dtype dtype, const lak_cfg *cfg);
+
+/*
+ * dense_gemv: y = A x for an m-by-n matrix  (Sec. 2's matrix-vector product,
+ * where work-group i forms the inner product of row i with the right-hand
+ * side; the column-major layout is this library's addition).
+ *   LAK_ROW_MAJOR: A(i,j) = A[i*lda + j], lda >= max(1, n).  A group of
+ *     threads per row (sized from n) reduces with shuffles.
+ *   LAK_COL_MAJOR: A(i,j) = A[i + j*lda], lda >= max(1, m).  Each thread owns
+ *     `vec` consecutive rows and sweeps columns; wide matrices are split over
+ *     columns (split-K), the partials land in `workspace` and the last block
+ *     of each row tile adds them in split order (deterministic).  Called on
+ *     the storage of a row-major matrix B (n-by-m) with layout COL_MAJOR this
+ *     computes B^T x.
+ * y has m elements, x has n.  `workspace` (>= dense_gemv_workspace() bytes,
+ * zero-filled before first use, left reusable by every completed call) may be
+ * NULL when the query returns 0.  m = 0 is a no-op; n = 0 writes y = 0.
+ */
+LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m,
+                              int64_t n, int64_t lda, lak_layout layout,
+                              lak_dtype dtype, void *workspace, size_t ws_bytes,
+                              const lak_cfg *cfg, void *stream);
+
+/*
+ * csr_spmv: y[i] = sum_{k=row_ptr[i]}^{row_ptr[i+1]-1} vals[k] * x[col_idx[k]]
+ * for an m-by-n CSR matrix with nnz stored entries (textbook CSR product; the
+ * paper leaves sparse formats out of its study, Sec. 1).  A group of
+ * 1..32 lanes per row, sized from the mean row length nnz/m, walks the row's
+ * entries and reduces with shuffles.  Requirements the library does not check
+ * on the device: row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[m] = nnz,
+ * 0 <= col_idx[k] < n.  Repeated columns in a row are summed.  m = 0 is a
+ * no-op; empty rows give 0.
+ */
+LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_idx,
+                            const void *vals, const void *x, int64_t m, int64_t n,
+                            int64_t nnz, lak_dtype dtype, const lak_cfg *cfg,
+                            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAK_H */

@@ -1,0 +1,263 @@
+"""GB300 (sm_103a) library of memory-bandwidth-bound linear-algebra kernels.
+
+The operations of Rupp et al., "Performance Portability Study of Linear
+Algebra Kernels in OpenCL" (IWOCL'14, Sec. 2) -- vector copy, vector update
+x = y + alpha*z, inner product <x, y>, dense matrix-vector product in row- and
+column-major layouts -- plus the CSR sparse matrix-vector product, as
+hand-written CUDA kernels behind the C ABI of ``include/lak.h``.
+
+This module is the thin Python binding: it checks tensor devices, dtypes and
+strides, turns tensors into raw device pointers and calls the C entry points of
+the same names on the current CUDA stream.  Every arithmetic step runs in the
+CUDA library; PyTorch only supplies device memory and streams.  Workspace for
+the calls that need it is kept per (device, stream), zero-filled when first
+allocated, which is the state the kernels require and leave behind.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Union
+
+import torch
+
+from . import _native
+from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
+
+__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "dense_gemv",
+           "dense_gemv_workspace", "csr_spmv", "resolve_cfg", "set_default_cfg", "Cfg",
+           "LakError", "storage_of", "library_path"]
+
+_lib = _native.load()
+
+_TORCH_TO_STORAGE = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16",
+                     torch.float16: "f16"}
+
+CfgLike = Union[None, LakCfg, Sequence[int], dict]
+
+
+def library_path() -> str:
+    return _native.LIB_PATH
+
+
+def Cfg(block: int = 0, grid: int = 0, vec: int = 0, increment: Union[int, str] = 0) -> LakCfg:
+    """A launch configuration (Sec. 2's local size, work-groups, vector
+    length, increment type); zeros mean automatic."""
+    inc = INCREMENTS[increment] if isinstance(increment, str) else int(increment)
+    return LakCfg(int(block), int(grid), int(vec), inc)
+
+
+def _cfg_ptr(cfg: CfgLike):
+    if cfg is None:
+        return None
+    if isinstance(cfg, LakCfg):
+        c = cfg
+    elif isinstance(cfg, dict):
+        c = Cfg(**cfg)
+    else:
+        c = Cfg(*cfg)
+    return ctypes.byref(c)
+
+
+def storage_of(t: torch.Tensor) -> str:
+    try:
+        return _TORCH_TO_STORAGE[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {t.dtype}; expected float32/float64/bfloat16/float16")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev_ptr(t: torch.Tensor, name: str) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t.data_ptr()
+
+
+def _vec_arg(t: torch.Tensor, name: str):
+    if t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1):
+        raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    return _dev_ptr(t, name)
+
+
+def _same_storage(*ts):
+    s = storage_of(ts[0])
+    for t in ts[1:]:
+        if t.dtype != ts[0].dtype:
+            raise TypeError("all operands must share one dtype")
+        if t.device != ts[0].device:
+            raise ValueError("all operands must be on one device")
+    return s
+
+
+# ---- workspace -------------------------------------------------------------------
+
+_workspaces = {}
+
+
+def _workspace(nbytes: int, stream_handle: int, device: torch.device) -> torch.Tensor:
+    """Zero-filled scratch kept per (device, stream); grown (and re-zeroed)
+    when a call needs more.  Kernels leave their counters at zero."""
+    key = (device.index, stream_handle)
+    ws = _workspaces.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.zeros(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _workspaces[key] = ws
+    return ws
+
+
+# ---- entry points ----------------------------------------------------------------
+
+def resolve_cfg(op: str, storage: str, m: int, n: int = 0, nnz: int = 0,
+                cfg: CfgLike = None) -> LakCfg:
+    """The launch configuration the library would use (lak_resolve_cfg)."""
+    out = LakCfg()
+    st = _lib.lak_resolve_cfg(OPS[op], DTYPES[storage], int(m), int(n), int(nnz), _cfg_ptr(cfg),
+                              ctypes.byref(out))
+    _native.check("lak_resolve_cfg", st)
+    return out
+
+
+def set_default_cfg(op: str, storage: str, cfg: CfgLike):
+    """Replace (or with cfg=None restore) the default configuration of an op."""
+    _native.check("lak_set_default_cfg",
+                  _lib.lak_set_default_cfg(OPS[op], DTYPES[storage], _cfg_ptr(cfg)))
+
+
+def vec_copy(x: torch.Tensor, y: torch.Tensor, cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """x[:] = y (bit copy)."""
+    s = _same_storage(x, y)
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same length")
+    st = _lib.vec_copy(_vec_arg(x, "x"), _vec_arg(y, "y"), x.numel(), DTYPES[s], _cfg_ptr(cfg),
+                       _stream(stream))
+    _native.check("vec_copy", st)
+    return x
+
+
+def vec_axpy(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, alpha: float,
+             cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """x[:] = y + alpha * z."""
+    s = _same_storage(x, y, z)
+    n = x.numel()
+    if y.numel() != n or z.numel() != n:
+        raise ValueError("x, y, z must have the same length")
+    st = _lib.vec_axpy(_vec_arg(x, "x"), _vec_arg(y, "y"), _vec_arg(z, "z"), float(alpha), n,
+                       DTYPES[s], _cfg_ptr(cfg), _stream(stream))
+    _native.check("vec_axpy", st)
+    return x
+
+
+def vec_dot_workspace(n: int, storage: str, cfg: CfgLike = None) -> int:
+    return int(_lib.vec_dot_workspace(int(n), DTYPES[storage], _cfg_ptr(cfg)))
+
+
+def vec_dot(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None,
+            workspace: Optional[torch.Tensor] = None, cfg: CfgLike = None,
+            stream=None) -> torch.Tensor:
+    """<x, y> into a one-element device tensor (float32 for FP32/BF16/FP16
+    storage, float64 for FP64)."""
+    s = _same_storage(x, y)
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    odt = torch.float64 if s == "f64" else torch.float32
+    if out is None:
+        out = torch.empty(1, dtype=odt, device=x.device)
+    elif out.dtype != odt or out.numel() < 1:
+        raise TypeError(f"out must be a {odt} tensor with at least one element")
+    sh = _stream(stream)
+    need = vec_dot_workspace(n, s, cfg)
+    if workspace is None:
+        workspace = _workspace(need, sh, x.device)
+    st = _lib.vec_dot(_dev_ptr(out, "out"), _vec_arg(x, "x"), _vec_arg(y, "y"), n, DTYPES[s],
+                      _dev_ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                      _cfg_ptr(cfg), sh)
+    _native.check("vec_dot", st)
+    return out
+
+
+def dense_gemv_workspace(m: int, n: int, layout: str, storage: str, cfg: CfgLike = None) -> int:
+    return int(_lib.dense_gemv_workspace(int(m), int(n), LAYOUTS[layout], DTYPES[storage],
+                                         _cfg_ptr(cfg)))
+
+
+def _matrix_layout(A: torch.Tensor):
+    """(m, n, lda, layout) of a 2-D tensor viewed as a row- or column-major matrix."""
+    if A.dim() != 2:
+        raise ValueError("A must be 2-D (or pass m, n, lda and layout with a 1-D buffer)")
+    m, n = A.shape
+    s0, s1 = A.stride()
+    if s1 == 1 and (m <= 1 or s0 >= max(n, 1)):
+        return m, n, (s0 if m > 1 else max(n, 1)), "row"
+    if s0 == 1 and (n <= 1 or s1 >= max(m, 1)):
+        return m, n, (s1 if n > 1 else max(m, 1)), "col"
+    raise ValueError("A must have unit stride along one dimension")
+
+
+def dense_gemv(A: torch.Tensor, x: torch.Tensor, y: Optional[torch.Tensor] = None,
+               m: Optional[int] = None, n: Optional[int] = None, lda: Optional[int] = None,
+               layout: Optional[str] = None, workspace: Optional[torch.Tensor] = None,
+               cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """y = A x.  A is a 2-D tensor (its strides give the layout and lda), or a
+    1-D buffer with explicit m, n, lda and layout ('row' or 'col')."""
+    s = _same_storage(A, x)
+    if A.dim() == 2 and m is None:
+        m, n, lda, lay = _matrix_layout(A)
+        if layout is not None and layout != lay:
+            raise ValueError(f"A's strides give layout {lay!r}, not {layout!r}")
+        layout = lay
+    else:
+        if None in (m, n, lda, layout):
+            raise ValueError("a 1-D matrix buffer needs m, n, lda and layout")
+    if layout not in LAYOUTS:
+        raise ValueError(f"layout must be 'row' or 'col', not {layout!r}")
+    if x.numel() != n:
+        raise ValueError(f"x has {x.numel()} elements, expected n={n}")
+    if y is None:
+        y = torch.empty(m, dtype=A.dtype, device=A.device)
+    elif y.dtype != A.dtype or y.numel() != m:
+        raise ValueError("y must match A's dtype and have m elements")
+    sh = _stream(stream)
+    need = dense_gemv_workspace(m, n, layout, s, cfg)
+    ws_ptr, ws_bytes = None, 0
+    if need > 0:
+        if workspace is None:
+            workspace = _workspace(need, sh, A.device)
+        ws_ptr = _dev_ptr(workspace, "workspace")
+        ws_bytes = workspace.numel() * workspace.element_size()
+    st = _lib.dense_gemv(_vec_arg(y, "y"), _dev_ptr(A, "A"), _vec_arg(x, "x"), int(m), int(n),
+                         int(lda), LAYOUTS[layout], DTYPES[s], ws_ptr, ws_bytes, _cfg_ptr(cfg), sh)
+    _native.check("dense_gemv", st)
+    return y
+
+
+def csr_spmv(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor, x: torch.Tensor,
+             y: Optional[torch.Tensor] = None, n_cols: Optional[int] = None,
+             cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """y = A x for A in CSR form (int32 row_ptr of m+1 entries, int32 col_idx)."""
+    s = _same_storage(vals, x)
+    if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+        raise TypeError("row_ptr and col_idx must be int32")
+    m = row_ptr.numel() - 1
+    if m < 0:
+        raise ValueError("row_ptr needs m+1 >= 1 entries")
+    nnz = vals.numel()
+    if col_idx.numel() != nnz:
+        raise ValueError("col_idx and vals must have nnz entries each")
+    n = x.numel() if n_cols is None else int(n_cols)
+    if y is None:
+        y = torch.empty(m, dtype=vals.dtype, device=vals.device)
+    elif y.dtype != vals.dtype or y.numel() != m:
+        raise ValueError("y must match vals' dtype and have m elements")
+    st = _lib.csr_spmv(_vec_arg(y, "y"), _vec_arg(row_ptr, "row_ptr"),
+                       _vec_arg(col_idx, "col_idx") if nnz else None,
+                       _vec_arg(vals, "vals") if nnz else None, _vec_arg(x, "x") if n else None,
+                       m, n, nnz, DTYPES[s], _cfg_ptr(cfg), _stream(stream))
+    _native.check("csr_spmv", st)
+    return y

@@ -1,0 +1,95 @@
+"""ctypes binding of the C ABI declared in include/lak.h.
+
+Loads the in-tree ``liblak_gb300.so``; importing fails loudly if it has not
+been built (there is no fallback implementation of any operation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblak_gb300.so")
+
+# enums of lak.h
+LAK_OK, LAK_EINVAL, LAK_EDTYPE, LAK_ELAYOUT, LAK_ECUDA, LAK_EWORKSPACE = 0, -1, -2, -3, -4, -5
+STATUS_NAMES = {0: "LAK_OK", -1: "LAK_EINVAL", -2: "LAK_EDTYPE", -3: "LAK_ELAYOUT",
+                -4: "LAK_ECUDA", -5: "LAK_EWORKSPACE"}
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
+LAYOUTS = {"row": 0, "col": 1}
+INCREMENTS = {"global": 0, "local": 1}
+OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
+
+# exported symbols, in header order (checked by the ABI test)
+EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
+           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "dense_gemv_workspace",
+           "dense_gemv", "csr_spmv")
+
+
+class LakCfg(ctypes.Structure):
+    """lak_cfg: (block, grid, vec, increment); zero fields mean automatic."""
+    _fields_ = [("block", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("vec", ctypes.c_int32), ("increment", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.block, self.grid, self.vec, self.increment)
+
+    def __repr__(self):
+        return "LakCfg(block=%d, grid=%d, vec=%d, increment=%d)" % self.as_tuple()
+
+
+class LakError(RuntimeError):
+    def __init__(self, fn: str, status: int, message: str):
+        self.status = status
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SZ = ctypes.c_size_t
+_CFGP = ctypes.POINTER(LakCfg)
+
+_SIGNATURES = {
+    "lak_last_error": (ctypes.c_char_p, []),
+    "lak_abi_version": (_I32, []),
+    "lak_set_default_cfg": (_I32, [_I32, _I32, _CFGP]),
+    "lak_resolve_cfg": (_I32, [_I32, _I32, _I64, _I64, _I64, _CFGP, _CFGP]),
+    "vec_copy": (_I32, [_P, _P, _I64, _I32, _CFGP, _P]),
+    "vec_axpy": (_I32, [_P, _P, _P, ctypes.c_double, _I64, _I32, _CFGP, _P]),
+    "vec_dot_workspace": (_SZ, [_I64, _I32, _CFGP]),
+    "vec_dot": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
+    "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
+    "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
+    "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library and declare the C signatures (idempotent)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().lak_last_error().decode(errors="replace")
+
+
+def check(fn: str, status: int):
+    if status != LAK_OK:
+        raise LakError(fn, status, last_error())

@@ -1,0 +1,271 @@
+// Vector kernels: copy x <- y, update x <- y + alpha*z, inner product <x, y>
+// (Rupp et al., IWOCL'14, Sec. 2).  All three share the two loop skeletons
+// of Sec. 2 -- "global increment" (grid-stride) and "local increment" (each
+// block walks its own contiguous range) -- and the vector length of Sec. 2,
+// realised as V consecutive elements per thread read with the widest aligned
+// loads (up to 256-bit on sm_103a).  A scalar prologue/epilogue covers the
+// elements before the first aligned address and after the last full group.
+#include "lak_internal.cuh"
+
+namespace lak {
+namespace {
+
+// Chunk range of this thread under the two skeletons.
+struct Range {
+    int64_t begin, end, stride;
+};
+
+__device__ __forceinline__ Range chunk_range(int64_t nchunks, int inc) {
+    Range r;
+    if (inc == LAK_INC_GLOBAL) {
+        r.begin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        r.end = nchunks;
+        r.stride = (int64_t)gridDim.x * blockDim.x;
+    } else {
+        // block b owns chunks [b*per, (b+1)*per); per is a multiple of the block
+        // size so that every block starts on a whole-block boundary
+        int64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
+        per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+        int64_t b0 = (int64_t)blockIdx.x * per;
+        r.begin = b0 + threadIdx.x;
+        r.end = b0 + per < nchunks ? b0 + per : nchunks;
+        r.stride = blockDim.x;
+    }
+    return r;
+}
+
+// Index of the t-th element outside the vectorised body (prologue, then tail).
+__device__ __forceinline__ int64_t extra_index(int64_t t, int64_t head, int64_t body_end) {
+    return t < head ? t : body_end + (t - head);
+}
+
+// ---- copy: a bit copy of elements of 2, 4 or 8 bytes ----------------------
+
+template <typename E, int V>
+__global__ void __launch_bounds__(512)
+copy_kernel(E *__restrict__ x, const E *__restrict__ y, int64_t n, int64_t head,
+            int64_t nchunks, int inc) {
+    const E *yb = y + head;
+    E *xb = x + head;
+    const Range r = chunk_range(nchunks, inc);
+    for (int64_t c = r.begin; c < r.end; c += r.stride) {
+        Pack<E, V> p;
+        load_pack<E, V, STREAM>(p, yb + c * V);
+        store_pack<E, V>(xb + c * V, p);
+    }
+    const int64_t body_end = head + nchunks * V;
+    const int64_t nextra = head + (n - body_end);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nextra) {
+        const int64_t i = extra_index(t, head, body_end);
+        x[i] = y[i];
+    }
+}
+
+// ---- axpy: x = y + alpha*z, one fused multiply-add per element -------------
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+axpy_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, int64_t n, int64_t head,
+            int64_t nchunks, int inc) {
+    // x may alias y or z, so the loads take the coherent path
+    const Range r = chunk_range(nchunks, inc);
+    for (int64_t c = r.begin; c < r.end; c += r.stride) {
+        const int64_t o = head + c * V;
+        Pack<T, V> py, pz, px;
+        load_pack<T, V, COHERENT>(py, y + o);
+        load_pack<T, V, COHERENT>(pz, z + o);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            px.e[v] = narrow<T>(fma_acc(alpha, widen(pz.e[v]), widen(py.e[v])));
+        store_pack<T, V>(x + o, px);
+    }
+    const int64_t body_end = head + nchunks * V;
+    const int64_t nextra = head + (n - body_end);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nextra) {
+        const int64_t i = extra_index(t, head, body_end);
+        x[i] = narrow<T>(fma_acc(alpha, widen(z[i]), widen(y[i])));
+    }
+}
+
+// ---- dot: single pass, last-arriving block combines -------------------------
+//
+// Per thread: V independent accumulators in the arithmetic type (FP32 for
+// FP32/BF16/FP16 storage).  Per warp: shuffle tree.  Per block: the warp sums
+// are added in FP64 and the block partial is stored in the workspace.  The
+// block whose arrival ticket is last adds all partials in FP64 in a fixed
+// order (strided per thread, then a shuffle tree), so the result does not
+// depend on which block happens to arrive last.  The ticket uses atomicInc
+// with wrap-around at gridDim.x - 1, so a completed call leaves the counter at
+// zero for the next call.
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+dot_kernel(void *out, const T *__restrict__ x, const T *__restrict__ y, int64_t n,
+           int64_t head, int64_t nchunks, int inc, unsigned int *counter,
+           double *partials) {
+    using A = typename Acc<T>::type;
+    __shared__ double wsum[32];
+    __shared__ int am_last;
+
+    A acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = A(0);
+
+    const Range r = chunk_range(nchunks, inc);
+    for (int64_t c = r.begin; c < r.end; c += r.stride) {
+        const int64_t o = head + c * V;
+        Pack<T, V> px, py;
+        load_pack<T, V, STREAM>(px, x + o);
+        load_pack<T, V, STREAM>(py, y + o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma_acc(widen(px.e[v]), widen(py.e[v]), acc[v]);
+    }
+    {
+        const int64_t body_end = head + nchunks * V;
+        const int64_t nextra = head + (n - body_end);
+        const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < nextra) {
+            const int64_t i = extra_index(t, head, body_end);
+            acc[0] = fma_acc(widen(x[i]), widen(y[i]), acc[0]);
+        }
+    }
+    // pairwise combine of the thread's accumulators
+#pragma unroll
+    for (int w = 1; w < V; w <<= 1) {
+#pragma unroll
+        for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+    }
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    A s = group_sum(acc[0], 32);
+    if (lane == 0) wsum[warp] = (double)s;
+    __syncthreads();
+    if (warp == 0) {
+        double b = lane < nwarps ? wsum[lane] : 0.0;
+        b = group_sum(b, 32);
+        if (lane == 0) {
+            partials[blockIdx.x] = b;
+            __threadfence();
+            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
+            am_last = (ticket == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!am_last) return;
+
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
+    v = group_sum(v, 32);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double f = lane < nwarps ? wsum[lane] : 0.0;
+        f = group_sum(f, 32);
+        if (lane == 0) {
+            if constexpr (sizeof(A) == 8)
+                *static_cast<double *>(out) = f;
+            else
+                *static_cast<float *>(out) = __double2float_rn(f);
+        }
+    }
+}
+
+// ---- dispatch ----------------------------------------------------------------
+
+template <typename E>
+lak_status copy_vec(int vec, E *x, const E *y, int64_t n, int64_t head, const Launch &L,
+                    cudaStream_t s) {
+    const int64_t nchunks = (n - head) / vec;
+    switch (vec) {
+    case 1: copy_kernel<E, 1><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    case 2: copy_kernel<E, 2><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    case 4: copy_kernel<E, 4><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    case 8: copy_kernel<E, 8><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    case 16: copy_kernel<E, 16><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    default: return fail(LAK_EINVAL, "vec_copy: unsupported vec %d", vec);
+    }
+    return check_launch("vec_copy");
+}
+
+template <typename T>
+lak_status axpy_t(int vec, void *x, const void *y, const void *z, double alpha, int64_t n,
+                  int64_t head, const Launch &L, cudaStream_t s) {
+    using A = typename Acc<T>::type;
+    T *xp = static_cast<T *>(x);
+    const T *yp = static_cast<const T *>(y);
+    const T *zp = static_cast<const T *>(z);
+    const A a = static_cast<A>(alpha);
+    const int64_t nchunks = (n - head) / vec;
+    switch (vec) {
+    case 1: axpy_kernel<T, 1><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 2: axpy_kernel<T, 2><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 4: axpy_kernel<T, 4><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 8: axpy_kernel<T, 8><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 16: axpy_kernel<T, 16><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    default: return fail(LAK_EINVAL, "vec_axpy: unsupported vec %d", vec);
+    }
+    return check_launch("vec_axpy");
+}
+
+template <typename T>
+lak_status dot_t(int vec, void *out, const void *x, const void *y, int64_t n, int64_t head,
+                 void *ws, const Launch &L, cudaStream_t s) {
+    const T *xp = static_cast<const T *>(x);
+    const T *yp = static_cast<const T *>(y);
+    unsigned int *counter = static_cast<unsigned int *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 8);
+    const int64_t nchunks = (n - head) / vec;
+#define LAK_DOT(VV)                                                                     \
+    dot_kernel<T, VV><<<L.grid, L.block, 0, s>>>(out, xp, yp, n, head, nchunks, L.inc, \
+                                                 counter, partials)
+    switch (vec) {
+    case 1: LAK_DOT(1); break;
+    case 2: LAK_DOT(2); break;
+    case 4: LAK_DOT(4); break;
+    case 8: LAK_DOT(8); break;
+    case 16: LAK_DOT(16); break;
+    default: return fail(LAK_EINVAL, "vec_dot: unsupported vec %d", vec);
+    }
+#undef LAK_DOT
+    return check_launch("vec_dot");
+}
+
+}  // namespace
+
+lak_status launch_copy(void *x, const void *y, int64_t n, int es, const Launch &L, int64_t head,
+                       cudaStream_t s) {
+    switch (es) {
+    case 2: return copy_vec<uint16_t>(L.vec, (uint16_t *)x, (const uint16_t *)y, n, head, L, s);
+    case 4: return copy_vec<uint32_t>(L.vec, (uint32_t *)x, (const uint32_t *)y, n, head, L, s);
+    case 8: return copy_vec<uint64_t>(L.vec, (uint64_t *)x, (const uint64_t *)y, n, head, L, s);
+    }
+    return fail(LAK_EDTYPE, "vec_copy: element size %d", es);
+}
+
+lak_status launch_axpy(lak_dtype dt, void *x, const void *y, const void *z, double alpha,
+                       int64_t n, const Launch &L, int64_t head, cudaStream_t s) {
+    switch (dt) {
+    case LAK_F32: return axpy_t<float>(L.vec, x, y, z, alpha, n, head, L, s);
+    case LAK_F64: return axpy_t<double>(L.vec, x, y, z, alpha, n, head, L, s);
+    case LAK_BF16: return axpy_t<__nv_bfloat16>(L.vec, x, y, z, alpha, n, head, L, s);
+    case LAK_F16: return axpy_t<__half>(L.vec, x, y, z, alpha, n, head, L, s);
+    }
+    return fail(LAK_EDTYPE, "vec_axpy: unknown dtype %d", (int)dt);
+}
+
+lak_status launch_dot(lak_dtype dt, void *out, const void *x, const void *y, int64_t n, void *ws,
+                      const Launch &L, int64_t head, cudaStream_t s) {
+    switch (dt) {
+    case LAK_F32: return dot_t<float>(L.vec, out, x, y, n, head, ws, L, s);
+    case LAK_F64: return dot_t<double>(L.vec, out, x, y, n, head, ws, L, s);
+    case LAK_BF16: return dot_t<__nv_bfloat16>(L.vec, out, x, y, n, head, ws, L, s);
+    case LAK_F16: return dot_t<__half>(L.vec, out, x, y, n, head, ws, L, s);
+    }
+    return fail(LAK_EDTYPE, "vec_dot: unknown dtype %d", (int)dt);
+}
+
+}  // namespace lak

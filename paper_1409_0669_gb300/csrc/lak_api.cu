@@ -1,0 +1,530 @@
+// The C ABI (include/lak.h): argument checks, launch-configuration resolution
+// (defaults, automatic grid / vector width / group size), workspace sizing and
+// dispatch to the kernel launchers.  Host code only.
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "lak_internal.cuh"
+
+namespace lak {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local char g_msg[512] = "";
+
+lak_status fail(lak_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lak_status check_launch(const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(LAK_ECUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
+    return LAK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device facts
+// ---------------------------------------------------------------------------
+
+namespace {
+constexpr int kMaxDevices = 64;
+DeviceInfo g_dev[kMaxDevices];
+bool g_dev_ok[kMaxDevices];
+std::mutex g_dev_mu;
+}  // namespace
+
+const DeviceInfo *device_info() {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) {
+        fail(LAK_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    if (d < 0 || d >= kMaxDevices) {
+        fail(LAK_ECUDA, "device ordinal %d out of range", d);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_dev_ok[d]) {
+        DeviceInfo di{};
+        di.device = d;
+        e = cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, d);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&di.max_threads_per_sm,
+                                       cudaDevAttrMaxThreadsPerMultiProcessor, d);
+        if (e != cudaSuccess) {
+            fail(LAK_ECUDA, "device attributes: %s", cudaGetErrorString(e));
+            return nullptr;
+        }
+        g_dev[d] = di;
+        g_dev_ok[d] = true;
+    }
+    return &g_dev[d];
+}
+
+// ---------------------------------------------------------------------------
+// configuration
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Built-in defaults per op: the paper's GPU guideline (Sec. 4: 128 or 256
+// work items per group, many groups, global increment on GPUs), with the
+// per-thread vector width set to the widest single load for the storage type.
+lak_cfg builtin_default(lak_op op, lak_dtype dt) {
+    const int es = esize(dt);
+    lak_cfg c{256, 0, 0, LAK_INC_GLOBAL};
+    switch (op) {
+    case LAK_OP_COPY:
+    case LAK_OP_AXPY:
+    case LAK_OP_DOT: c.vec = 32 / es; break;           // one 256-bit access
+    case LAK_OP_GEMV_ROW: c.vec = 16 / es; break;      // one 128-bit access
+    case LAK_OP_GEMV_COL: c.vec = 16 / es; break;
+    case LAK_OP_SPMV: c.vec = 2; break;
+    default: break;
+    }
+    return c;
+}
+
+lak_cfg g_override[LAK_OP_COUNT][4];
+bool g_has_override[LAK_OP_COUNT][4];
+std::mutex g_cfg_mu;
+
+bool valid_dtype(lak_dtype dt) { return dt == LAK_F32 || dt == LAK_F64 || dt == LAK_BF16 || dt == LAK_F16; }
+bool valid_op(lak_op op) { return op >= 0 && op < LAK_OP_COUNT; }
+bool pow2_vec(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; }
+
+lak_status check_cfg(const lak_cfg *c, const char *who) {
+    if (!c || c->block == 0) return LAK_OK;
+    if (c->block < 32 || c->block > 512 || c->block % 32)
+        return fail(LAK_EINVAL, "%s: cfg.block=%d must be a multiple of 32 in [32, 512]", who, c->block);
+    if (c->grid < 0) return fail(LAK_EINVAL, "%s: cfg.grid=%d must be >= 0", who, c->grid);
+    if (c->vec != 0 && !pow2_vec(c->vec))
+        return fail(LAK_EINVAL, "%s: cfg.vec=%d must be 0, 1, 2, 4, 8 or 16", who, c->vec);
+    if (c->increment != LAK_INC_GLOBAL && c->increment != LAK_INC_LOCAL)
+        return fail(LAK_EINVAL, "%s: cfg.increment=%d must be 0 (global) or 1 (local)", who,
+                    c->increment);
+    return LAK_OK;
+}
+
+// Explicit cfg, else the override table, else the built-in default; zero
+// grid / vec fields stay zero here (filled per op below).
+lak_cfg base_cfg(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
+    if (cfg && cfg->block != 0) return *cfg;
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    if (g_has_override[op][dt]) return g_override[op][dt];
+    return builtin_default(op, dt);
+}
+
+int pow2_floor(int64_t v) {
+    int p = 1;
+    while ((int64_t)p * 2 <= v && p < (1 << 30)) p *= 2;
+    return p;
+}
+
+// largest power of two dividing the block size (groups must tile the block)
+int block_pow2(int block) { return block & -block; }
+
+int waves_grid(const DeviceInfo *di, int block) {
+    int per_sm = di->max_threads_per_sm / block;
+    if (per_sm < 1) per_sm = 1;
+    return di->sms * per_sm;
+}
+
+struct VecPlan {
+    Launch L;
+    int64_t head;
+};
+
+lak_status plan_vector(lak_op op, lak_dtype dt, int64_t n, const lak_cfg *cfg,
+                       const void *const *ptrs, int nptrs, VecPlan *out) {
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    lak_cfg c = base_cfg(op, dt, cfg);
+    const int es = esize(dt);
+    int want = c.vec ? c.vec : builtin_default(op, dt).vec;
+    int64_t head = 0;
+    int vec = ptrs ? pick_vec(want, es, ptrs, nptrs, n, &head) : want;
+    const int64_t nchunks = vec > 0 ? (n - head) / vec : n;
+    int64_t grid = c.grid;
+    if (grid == 0) {
+        const int64_t need = ceil_div(nchunks > 0 ? nchunks : 1, c.block);
+        const int64_t cap = waves_grid(di, c.block);
+        grid = need < cap ? need : cap;
+    }
+    if (grid < 1) grid = 1;
+    if (grid > 0x7fffffff) grid = 0x7fffffff;
+    out->L = Launch{c.block, (int)grid, vec, c.increment};
+    out->head = head;
+    return LAK_OK;
+}
+
+struct RowPlan {
+    Launch L;
+    int group;
+};
+
+// Row-major GEMV: group size G grows with the row length (each lane should
+// see at least 4 V-groups), limited by the block.
+lak_status plan_gemv_row(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const lak_cfg *cfg,
+                         const void *A, const void *x, RowPlan *out) {
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    lak_cfg c = base_cfg(LAK_OP_GEMV_ROW, dt, cfg);
+    const int es = esize(dt);
+    int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_ROW, dt).vec;
+    // every row start and x must sit on the access width
+    while (vec > 1) {
+        const int w = access_bytes(vec, es);
+        const bool ok = (!A || (uintptr_t)A % w == 0) && (!x || (uintptr_t)x % w == 0) &&
+                        ((lda * es) % w == 0);
+        if (ok) break;
+        vec >>= 1;
+    }
+    const int64_t nch = n / vec;
+    int G = pow2_floor(nch / 4 > 0 ? nch / 4 : 1);
+    const int bp = block_pow2(c.block);
+    if (G > bp) G = bp;
+    const int R = c.block / G;
+    int64_t grid = c.grid;
+    if (grid == 0) grid = ceil_div(m > 0 ? m : 1, R);
+    if (grid > 0x7fffffff) grid = 0x7fffffff;
+    out->L = Launch{c.block, (int)grid, vec, c.increment};
+    out->group = G;
+    return LAK_OK;
+}
+
+struct ColPlan {
+    Launch L;
+    int splits;
+    int64_t tiles;
+    size_t ws_bytes;
+};
+
+lak_status plan_gemv_col(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const lak_cfg *cfg,
+                         const void *A, ColPlan *out) {
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dt, cfg);
+    const int es = esize(dt);
+    int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dt).vec;
+    while (vec > 1) {
+        const int w = access_bytes(vec, es);
+        if ((!A || (uintptr_t)A % w == 0) && ((lda * es) % w == 0)) break;
+        vec >>= 1;
+    }
+    const int64_t tiles = ceil_div(m > 0 ? m : 1, 32LL * vec);
+    const int nwarps = c.block / 32;
+    int64_t target = c.grid ? c.grid : 2LL * waves_grid(di, c.block);
+    int64_t splits = ceil_div(target, tiles);
+    const int64_t max_splits = n / (4LL * nwarps);      // >= 4 columns per warp per split
+    if (splits > max_splits) splits = max_splits;
+    if (splits > 65535) splits = 65535;
+    if (splits < 1) splits = 1;
+    const int acc_bytes = dt == LAK_F64 ? 8 : 4;
+    size_t ws = 0;
+    if (splits > 1) {
+        ws = (size_t)((tiles * 4 + 255) / 256 * 256) + (size_t)splits * (size_t)m * acc_bytes;
+    }
+    out->L = Launch{c.block, (int)(tiles * splits > 0x7fffffff ? 0x7fffffff : tiles * splits), vec,
+                    c.increment};
+    out->splits = (int)splits;
+    out->tiles = tiles;
+    out->ws_bytes = ws;
+    return LAK_OK;
+}
+
+struct SpmvPlan {
+    Launch L;
+    int group;
+};
+
+lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, SpmvPlan *out) {
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    lak_cfg c = base_cfg(LAK_OP_SPMV, dt, cfg);
+    int vec = c.vec ? c.vec : builtin_default(LAK_OP_SPMV, dt).vec;
+    const int64_t mean = m > 0 ? ceil_div(nnz, m) : 1;
+    // lanes per row: the power of two covering the mean row length in `vec`
+    // loads per lane, between 1 and a warp
+    int G = 1;
+    while (G < 32 && (int64_t)G * vec < mean) G *= 2;
+    const int bp = block_pow2(c.block);
+    if (G > bp) G = bp;
+    const int R = c.block / G;
+    int64_t grid = c.grid;
+    if (grid == 0) grid = ceil_div(m > 0 ? m : 1, R);
+    if (grid > 0x7fffffff) grid = 0x7fffffff;
+    out->L = Launch{c.block, (int)grid, vec, c.increment};
+    out->group = G;
+    return LAK_OK;
+}
+
+}  // namespace
+
+int pick_vec(int want, int es, const void *const *ptrs, int nptrs, int64_t n, int64_t *head) {
+    for (int vec = want; vec > 1; vec >>= 1) {
+        const int w = access_bytes(vec, es);
+        const uintptr_t off = (uintptr_t)ptrs[0] % w;
+        bool same = true;
+        for (int i = 1; i < nptrs; ++i)
+            if ((uintptr_t)ptrs[i] % w != off) same = false;
+        if (!same || off % es) continue;
+        int64_t h = (int64_t)((w - off) % w) / es;
+        if (h > n) h = n;
+        *head = h;
+        return vec;
+    }
+    *head = 0;
+    return 1;
+}
+
+}  // namespace lak
+
+using namespace lak;
+
+// ---------------------------------------------------------------------------
+// exported entry points
+// ---------------------------------------------------------------------------
+
+namespace {
+
+bool aligned_elem(const void *p, int es) { return (uintptr_t)p % (uintptr_t)es == 0; }
+
+lak_status common_checks(const char *who, lak_dtype dt, const lak_cfg *cfg) {
+    if (!valid_dtype(dt)) return fail(LAK_EDTYPE, "%s: unknown dtype %d", who, (int)dt);
+    return check_cfg(cfg, who);
+}
+
+}  // namespace
+
+extern "C" {
+
+LAK_API const char *lak_last_error(void) { return g_msg; }
+
+LAK_API int32_t lak_abi_version(void) { return 1; }
+
+LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg) {
+    if (!valid_op(op)) return fail(LAK_EINVAL, "lak_set_default_cfg: unknown op %d", (int)op);
+    if (!valid_dtype(dtype)) return fail(LAK_EDTYPE, "lak_set_default_cfg: unknown dtype %d", (int)dtype);
+    if (cfg && cfg->block == 0)
+        return fail(LAK_EINVAL, "lak_set_default_cfg: cfg.block must be set (or pass NULL)");
+    lak_status st = check_cfg(cfg, "lak_set_default_cfg");
+    if (st != LAK_OK) return st;
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    if (cfg) {
+        g_override[op][dtype] = *cfg;
+        g_has_override[op][dtype] = true;
+    } else {
+        g_has_override[op][dtype] = false;
+    }
+    return LAK_OK;
+}
+
+LAK_API lak_status lak_resolve_cfg(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz,
+                                   const lak_cfg *cfg, lak_cfg *out) {
+    if (!valid_op(op)) return fail(LAK_EINVAL, "lak_resolve_cfg: unknown op %d", (int)op);
+    lak_status st = common_checks("lak_resolve_cfg", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (!out || m < 0 || n < 0 || nnz < 0)
+        return fail(LAK_EINVAL, "lak_resolve_cfg: bad sizes or NULL out");
+    Launch L{};
+    switch (op) {
+    case LAK_OP_COPY:
+    case LAK_OP_AXPY:
+    case LAK_OP_DOT: {
+        VecPlan p;
+        st = plan_vector(op, dtype, m, cfg, nullptr, 0, &p);
+        L = p.L;
+        break;
+    }
+    case LAK_OP_GEMV_ROW: {
+        RowPlan p;
+        st = plan_gemv_row(dtype, m, n, n, cfg, nullptr, nullptr, &p);
+        L = p.L;
+        break;
+    }
+    case LAK_OP_GEMV_COL: {
+        ColPlan p;
+        st = plan_gemv_col(dtype, m, n, m, cfg, nullptr, &p);
+        L = p.L;
+        break;
+    }
+    case LAK_OP_SPMV: {
+        SpmvPlan p;
+        st = plan_spmv(dtype, m, nnz, cfg, &p);
+        L = p.L;
+        break;
+    }
+    default: return fail(LAK_EINVAL, "lak_resolve_cfg: unknown op");
+    }
+    if (st != LAK_OK) return st;
+    *out = lak_cfg{L.block, L.grid, L.vec, L.inc};
+    return LAK_OK;
+}
+
+LAK_API lak_status vec_copy(void *x, const void *y, int64_t n, lak_dtype dtype, const lak_cfg *cfg,
+                            void *stream) {
+    lak_status st = common_checks("vec_copy", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (n < 0) return fail(LAK_EINVAL, "vec_copy: n=%lld < 0", (long long)n);
+    if (n == 0) return LAK_OK;
+    const int es = esize(dtype);
+    if (!x || !y) return fail(LAK_EINVAL, "vec_copy: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es))
+        return fail(LAK_EINVAL, "vec_copy: pointers not aligned to the element size");
+    const void *ptrs[2] = {x, y};
+    VecPlan p;
+    st = plan_vector(LAK_OP_COPY, dtype, n, cfg, ptrs, 2, &p);
+    if (st != LAK_OK) return st;
+    return launch_copy(x, y, n, es, p.L, p.head, (cudaStream_t)stream);
+}
+
+LAK_API lak_status vec_axpy(void *x, const void *y, const void *z, double alpha, int64_t n,
+                            lak_dtype dtype, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_axpy", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (n < 0) return fail(LAK_EINVAL, "vec_axpy: n=%lld < 0", (long long)n);
+    if (n == 0) return LAK_OK;
+    const int es = esize(dtype);
+    if (!x || !y || !z) return fail(LAK_EINVAL, "vec_axpy: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es) || !aligned_elem(z, es))
+        return fail(LAK_EINVAL, "vec_axpy: pointers not aligned to the element size");
+    const void *ptrs[3] = {x, y, z};
+    VecPlan p;
+    st = plan_vector(LAK_OP_AXPY, dtype, n, cfg, ptrs, 3, &p);
+    if (st != LAK_OK) return st;
+    return launch_axpy(dtype, x, y, z, alpha, n, p.L, p.head, (cudaStream_t)stream);
+}
+
+LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg) {
+    if (!valid_dtype(dtype) || n < 0 || check_cfg(cfg, "vec_dot_workspace") != LAK_OK) return 0;
+    VecPlan p;
+    if (plan_vector(LAK_OP_DOT, dtype, n, cfg, nullptr, 0, &p) != LAK_OK) return 0;
+    // The grid never grows when alignment forces a narrower vec (fewer chunks
+    // per thread would need more blocks only without the cap): size for the
+    // widest grid any alignment of these n elements can produce.
+    VecPlan p1;
+    lak_cfg c = base_cfg(LAK_OP_DOT, dtype, cfg);
+    c.vec = 1;
+    if (plan_vector(LAK_OP_DOT, dtype, n, &c, nullptr, 0, &p1) != LAK_OK) return 0;
+    const int grid = p1.L.grid > p.L.grid ? p1.L.grid : p.L.grid;
+    return 8 + 8 * (size_t)grid;
+}
+
+LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n, lak_dtype dtype,
+                           void *workspace, size_t ws_bytes, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_dot", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (n < 0) return fail(LAK_EINVAL, "vec_dot: n=%lld < 0", (long long)n);
+    if (!out) return fail(LAK_EINVAL, "vec_dot: NULL out");
+    const int out_bytes = dtype == LAK_F64 ? 8 : 4;
+    if ((uintptr_t)out % out_bytes) return fail(LAK_EINVAL, "vec_dot: out misaligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        const cudaError_t e = cudaMemsetAsync(out, 0, out_bytes, s);
+        if (e != cudaSuccess) return fail(LAK_ECUDA, "vec_dot: memset: %s", cudaGetErrorString(e));
+        return LAK_OK;
+    }
+    const int es = esize(dtype);
+    if (!x || !y) return fail(LAK_EINVAL, "vec_dot: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es))
+        return fail(LAK_EINVAL, "vec_dot: pointers not aligned to the element size");
+    const void *ptrs[2] = {x, y};
+    VecPlan p;
+    st = plan_vector(LAK_OP_DOT, dtype, n, cfg, ptrs, 2, &p);
+    if (st != LAK_OK) return st;
+    const size_t need = 8 + 8 * (size_t)p.L.grid;
+    if (!workspace || ws_bytes < need)
+        return fail(LAK_EWORKSPACE, "vec_dot: workspace of %zu bytes needed, %zu given", need,
+                    workspace ? ws_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 8) return fail(LAK_EWORKSPACE, "vec_dot: workspace not 8-byte aligned");
+    return launch_dot(dtype, out, x, y, n, workspace, p.L, p.head, s);
+}
+
+LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout, lak_dtype dtype,
+                                    const lak_cfg *cfg) {
+    if (!valid_dtype(dtype) || m < 0 || n < 0 || check_cfg(cfg, "dense_gemv_workspace") != LAK_OK)
+        return 0;
+    if (layout != LAK_COL_MAJOR) return 0;
+    // the widest vec the call could pick gives the fewest tiles; narrower vecs
+    // (forced by alignment) only add tiles, so size for vec = 1 as well
+    size_t best = 0;
+    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dtype, cfg);
+    const int want = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dtype).vec;
+    for (int v = want; v >= 1; v >>= 1) {
+        lak_cfg cv = c;
+        cv.vec = v;
+        ColPlan p;
+        if (plan_gemv_col(dtype, m, n, m, &cv, nullptr, &p) != LAK_OK) return 0;
+        if (p.ws_bytes > best) best = p.ws_bytes;
+    }
+    return best;
+}
+
+LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m, int64_t n,
+                              int64_t lda, lak_layout layout, lak_dtype dtype, void *workspace,
+                              size_t ws_bytes, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("dense_gemv", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (layout != LAK_ROW_MAJOR && layout != LAK_COL_MAJOR)
+        return fail(LAK_ELAYOUT, "dense_gemv: unknown layout %d", (int)layout);
+    if (m < 0 || n < 0) return fail(LAK_EINVAL, "dense_gemv: negative size");
+    const int64_t ld_min = layout == LAK_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1);
+    if (lda < ld_min)
+        return fail(LAK_EINVAL, "dense_gemv: lda=%lld < %lld", (long long)lda, (long long)ld_min);
+    if (m == 0) return LAK_OK;
+    const int es = esize(dtype);
+    if (!y || (n > 0 && (!A || !x))) return fail(LAK_EINVAL, "dense_gemv: NULL pointer");
+    if (!aligned_elem(y, es) || !aligned_elem(A, es) || !aligned_elem(x, es))
+        return fail(LAK_EINVAL, "dense_gemv: pointers not aligned to the element size");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (layout == LAK_ROW_MAJOR) {
+        RowPlan p;
+        st = plan_gemv_row(dtype, m, n, lda, cfg, A, x, &p);
+        if (st != LAK_OK) return st;
+        return launch_gemv_row(dtype, y, A, x, m, n, lda, p.L, p.group, s);
+    }
+    ColPlan p;
+    st = plan_gemv_col(dtype, m, n, lda, cfg, A, &p);
+    if (st != LAK_OK) return st;
+    if (p.ws_bytes > 0) {
+        if (!workspace || ws_bytes < p.ws_bytes)
+            return fail(LAK_EWORKSPACE, "dense_gemv: workspace of %zu bytes needed, %zu given",
+                        p.ws_bytes, workspace ? ws_bytes : (size_t)0);
+        if ((uintptr_t)workspace % 256)
+            return fail(LAK_EWORKSPACE, "dense_gemv: workspace not 256-byte aligned");
+    }
+    return launch_gemv_col(dtype, y, A, x, m, n, lda, p.L, p.splits, workspace, s);
+}
+
+LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_idx,
+                            const void *vals, const void *x, int64_t m, int64_t n, int64_t nnz,
+                            lak_dtype dtype, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("csr_spmv", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (m < 0 || n < 0 || nnz < 0) return fail(LAK_EINVAL, "csr_spmv: negative size");
+    if (nnz > 0x7fffffffLL) return fail(LAK_EINVAL, "csr_spmv: nnz exceeds int32 indices");
+    if (m == 0) return LAK_OK;
+    const int es = esize(dtype);
+    if (!y || !row_ptr) return fail(LAK_EINVAL, "csr_spmv: NULL y or row_ptr");
+    if (nnz > 0 && (!col_idx || !vals || !x))
+        return fail(LAK_EINVAL, "csr_spmv: NULL col_idx, vals or x with nnz > 0");
+    if (!aligned_elem(y, es) || !aligned_elem(vals, es) || !aligned_elem(x, es) ||
+        !aligned_elem(row_ptr, 4) || !aligned_elem(col_idx, 4))
+        return fail(LAK_EINVAL, "csr_spmv: pointers not aligned to their element size");
+    SpmvPlan p;
+    st = plan_spmv(dtype, m, nnz, cfg, &p);
+    if (st != LAK_OK) return st;
+    return launch_spmv(dtype, y, row_ptr, col_idx, vals, x, m, p.L, p.group, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+// Internal declarations shared by the library's translation units: storage
+// type traits, wide load/store primitives (inline PTX, up to 256-bit), warp
+// reductions, the resolved launch description and host-side error helpers.
+// Nothing here is part of the C ABI (include/lak.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "lak.h"
+
+namespace lak {
+
+// ---------------------------------------------------------------------------
+// Host side: errors, device facts, resolved launch shape
+// ---------------------------------------------------------------------------
+
+// Records a printf-style message for lak_last_error() and returns `st`.
+lak_status fail(lak_status st, const char *fmt, ...);
+
+// Maps a pending launch error to LAK_ECUDA (message names `what`), else LAK_OK.
+lak_status check_launch(const char *what);
+
+struct DeviceInfo {
+    int device;
+    int sms;                 // streaming multiprocessors (152 on GB300)
+    int max_threads_per_sm;  // 2048 on sm_103a
+};
+
+// Facts about the current device, cached per device ordinal; nullptr (with
+// the message set) if the runtime cannot answer.
+const DeviceInfo *device_info();
+
+// A launch after defaults and automatic fields are filled in.
+struct Launch {
+    int block;   // threads per block
+    int grid;    // blocks (for column-major GEMV: total over both grid axes)
+    int vec;     // elements per access group (see lak_cfg)
+    int inc;     // LAK_INC_GLOBAL / LAK_INC_LOCAL
+};
+
+inline int esize(lak_dtype dt) {
+    switch (dt) {
+    case LAK_F32: return 4;
+    case LAK_F64: return 8;
+    case LAK_BF16: return 2;
+    case LAK_F16: return 2;
+    }
+    return 0;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Widest single access (bytes) used for a group of `vec` elements.
+inline int access_bytes(int vec, int es) {
+    int b = vec * es;
+    return b > 32 ? 32 : b;
+}
+
+// Largest vec <= want (power of two) whose access width divides the byte
+// offsets of every pointer in `ptrs` modulo the access width identically, so
+// that one scalar prologue aligns all of them at once.  Also returns the
+// prologue length (elements) in *head.
+int pick_vec(int want, int es, const void *const *ptrs, int nptrs, int64_t n, int64_t *head);
+
+// Launchers (one per kernel family), called after validation.
+lak_status launch_copy(void *x, const void *y, int64_t n, int es, const Launch &L,
+                       int64_t head, cudaStream_t s);
+lak_status launch_axpy(lak_dtype dt, void *x, const void *y, const void *z, double alpha,
+                       int64_t n, const Launch &L, int64_t head, cudaStream_t s);
+lak_status launch_dot(lak_dtype dt, void *out, const void *x, const void *y, int64_t n,
+                      void *ws, const Launch &L, int64_t head, cudaStream_t s);
+lak_status launch_gemv_row(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
+                           int64_t n, int64_t lda, const Launch &L, int group, cudaStream_t s);
+lak_status launch_gemv_col(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
+                           int64_t n, int64_t lda, const Launch &L, int splits, void *ws,
+                           cudaStream_t s);
+lak_status launch_spmv(lak_dtype dt, void *y, const int32_t *rp, const int32_t *ci,
+                       const void *vals, const void *x, int64_t m, const Launch &L, int group,
+                       cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device side: storage traits and conversions
+// ---------------------------------------------------------------------------
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T narrow(typename Acc<T>::type v);
+template <> __device__ __forceinline__ float narrow<float>(float v) { return v; }
+template <> __device__ __forceinline__ double narrow<double>(double v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half narrow<__half>(float v) { return __float2half_rn(v); }
+
+// fused multiply-add in the arithmetic type: one rounding
+__device__ __forceinline__ float fma_acc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_acc(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Device side: wide loads and stores
+// ---------------------------------------------------------------------------
+
+template <typename T, int V> struct Pack { T e[V]; };
+
+// Load policies.  STREAM: read-only path, no L1 allocation (data read once and
+// not written by the kernel).  COHERENT: ordinary coherent load, no L1
+// allocation (an output may alias this input).  CACHED: read-only path with
+// L1 allocation (operands many threads re-read, e.g. the GEMV right-hand side).
+enum { STREAM = 0, COHERENT = 1, CACHED = 2 };
+
+template <int B, int P> __device__ __forceinline__ void ld_raw(void *dst, const void *p);
+
+template <> __device__ __forceinline__ void ld_raw<2, STREAM>(void *dst, const void *p) {
+    unsigned short h;
+    asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(h) : "l"(p));
+    memcpy(dst, &h, 2);
+}
+template <> __device__ __forceinline__ void ld_raw<2, COHERENT>(void *dst, const void *p) {
+    unsigned short h;
+    asm("ld.global.L1::no_allocate.b16 %0, [%1];" : "=h"(h) : "l"(p));
+    memcpy(dst, &h, 2);
+}
+template <> __device__ __forceinline__ void ld_raw<4, STREAM>(void *dst, const void *p) {
+    uint32_t w;
+    asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p));
+    memcpy(dst, &w, 4);
+}
+template <> __device__ __forceinline__ void ld_raw<4, COHERENT>(void *dst, const void *p) {
+    uint32_t w;
+    asm("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(p));
+    memcpy(dst, &w, 4);
+}
+template <> __device__ __forceinline__ void ld_raw<8, STREAM>(void *dst, const void *p) {
+    uint32_t w[2];
+    asm("ld.global.nc.L1::no_allocate.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    memcpy(dst, w, 8);
+}
+template <> __device__ __forceinline__ void ld_raw<8, COHERENT>(void *dst, const void *p) {
+    uint32_t w[2];
+    asm("ld.global.L1::no_allocate.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    memcpy(dst, w, 8);
+}
+template <> __device__ __forceinline__ void ld_raw<16, STREAM>(void *dst, const void *p) {
+    uint32_t w[4];
+    asm("ld.global.nc.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+    memcpy(dst, w, 16);
+}
+template <> __device__ __forceinline__ void ld_raw<16, COHERENT>(void *dst, const void *p) {
+    uint32_t w[4];
+    asm("ld.global.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+    memcpy(dst, w, 16);
+}
+// 256-bit loads (sm_100 and later).
+template <> __device__ __forceinline__ void ld_raw<32, STREAM>(void *dst, const void *p) {
+    uint32_t w[8];
+    asm("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7])
+        : "l"(p));
+    memcpy(dst, w, 32);
+}
+template <> __device__ __forceinline__ void ld_raw<32, COHERENT>(void *dst, const void *p) {
+    uint32_t w[8];
+    asm("ld.global.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7])
+        : "l"(p));
+    memcpy(dst, w, 32);
+}
+
+template <> __device__ __forceinline__ void ld_raw<2, CACHED>(void *dst, const void *p) {
+    unsigned short h;
+    asm("ld.global.nc.b16 %0, [%1];" : "=h"(h) : "l"(p));
+    memcpy(dst, &h, 2);
+}
+template <> __device__ __forceinline__ void ld_raw<4, CACHED>(void *dst, const void *p) {
+    uint32_t w;
+    asm("ld.global.nc.b32 %0, [%1];" : "=r"(w) : "l"(p));
+    memcpy(dst, &w, 4);
+}
+template <> __device__ __forceinline__ void ld_raw<8, CACHED>(void *dst, const void *p) {
+    uint32_t w[2];
+    asm("ld.global.nc.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    memcpy(dst, w, 8);
+}
+template <> __device__ __forceinline__ void ld_raw<16, CACHED>(void *dst, const void *p) {
+    uint32_t w[4];
+    asm("ld.global.nc.v4.b32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+    memcpy(dst, w, 16);
+}
+template <> __device__ __forceinline__ void ld_raw<32, CACHED>(void *dst, const void *p) {
+    uint32_t w[8];
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7])
+        : "l"(p));
+    memcpy(dst, w, 32);
+}
+
+template <int B> __device__ __forceinline__ void st_raw(void *p, const void *src);
+template <> __device__ __forceinline__ void st_raw<2>(void *p, const void *src) {
+    unsigned short h;
+    memcpy(&h, src, 2);
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"(h));
+}
+template <> __device__ __forceinline__ void st_raw<4>(void *p, const void *src) {
+    uint32_t w;
+    memcpy(&w, src, 4);
+    asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(w));
+}
+template <> __device__ __forceinline__ void st_raw<8>(void *p, const void *src) {
+    uint32_t w[2];
+    memcpy(w, src, 8);
+    asm volatile("st.global.v2.b32 [%0], {%1,%2};" ::"l"(p), "r"(w[0]), "r"(w[1]));
+}
+template <> __device__ __forceinline__ void st_raw<16>(void *p, const void *src) {
+    uint32_t w[4];
+    memcpy(w, src, 16);
+    asm volatile("st.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]));
+}
+template <> __device__ __forceinline__ void st_raw<32>(void *p, const void *src) {
+    uint32_t w[8];
+    memcpy(w, src, 32);
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]));
+}
+
+// Load V consecutive elements starting at p (aligned to min(V*sizeof(T), 32)).
+template <typename T, int V, int P>
+__device__ __forceinline__ void load_pack(Pack<T, V> &pk, const T *p) {
+    constexpr int B = V * (int)sizeof(T);
+    if constexpr (B <= 32) {
+        ld_raw<B, P>(&pk, p);
+    } else {
+        static_assert(B % 32 == 0, "pack size");
+#pragma unroll
+        for (int c = 0; c < B / 32; ++c)
+            ld_raw<32, P>(reinterpret_cast<char *>(&pk) + 32 * c,
+                           reinterpret_cast<const char *>(p) + 32 * c);
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void store_pack(T *p, const Pack<T, V> &pk) {
+    constexpr int B = V * (int)sizeof(T);
+    if constexpr (B <= 32) {
+        st_raw<B>(p, &pk);
+    } else {
+#pragma unroll
+        for (int c = 0; c < B / 32; ++c)
+            st_raw<32>(reinterpret_cast<char *>(p) + 32 * c,
+                       reinterpret_cast<const char *>(&pk) + 32 * c);
+    }
+}
+
+// Cached (L1-allocating) read-only scalar load, for operands that many
+// threads re-read (the right-hand side x of GEMV / SpMV).
+template <typename T> __device__ __forceinline__ T ld_cached(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// Device side: reductions
+// ---------------------------------------------------------------------------
+
+// Sum over aligned groups of `width` lanes (width a power of two <= 32); every
+// lane of the warp must call it.  All lanes of a group end with the sum.
+template <typename A> __device__ __forceinline__ A group_sum(A v, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lak

@@ -219,3 +219,33 @@ def log_uniform_ints(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     g = rng(seed)
     v = np.exp(g.uniform(math.log(lo), math.log(hi + 1), size=count))
     return np.clip(np.floor(v).astype(np.int64), lo, hi)
+
+
+# ---- device-side generation (large benchmark inputs) -----------------------------
+#
+# The full-size sweep needs ~16 GB of inputs; drawing them on the host would
+# dominate the benchmark's set-up time.  These draw the same distributions on
+# the GPU with torch's counter-based Philox generator, seeded explicitly.
+
+def device_uniform_(out: torch.Tensor, seed: int, lo: float = -1.0, hi: float = 1.0):
+    """Fill `out` in place with U(lo, hi) values (Philox, seeded)."""
+    g = torch.Generator(device=out.device).manual_seed(seed)
+    if out.dtype in (torch.float32, torch.float64):
+        out.uniform_(lo, hi, generator=g)
+    else:
+        tmp = torch.empty(out.shape, dtype=torch.float32, device=out.device)
+        tmp.uniform_(lo, hi, generator=g)
+        out.copy_(tmp)
+    return out
+
+
+def device_normal_(out: torch.Tensor, seed: int):
+    """Fill `out` in place with N(0, 1) values (Philox, seeded)."""
+    g = torch.Generator(device=out.device).manual_seed(seed)
+    if out.dtype in (torch.float32, torch.float64):
+        out.normal_(0.0, 1.0, generator=g)
+    else:
+        tmp = torch.empty(out.shape, dtype=torch.float32, device=out.device)
+        tmp.normal_(0.0, 1.0, generator=g)
+        out.copy_(tmp)
+    return out

@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads on a machine without a GPU, and exports
+every entry point that include/lak.h declares; argument checks that return
+before any CUDA call behave as documented (no compute without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lak.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1409_0669_gb300 import _build
+    path = _build.build()
+    from paper_1409_0669_gb300 import _native
+    return _native.load(path)
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return re.findall(r"LAK_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("vec_axpy", "vec_dot", "dense_gemv", "csr_spmv"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1409_0669_gb300 import _native
+    so = _native.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in declared_symbols():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+    assert set(declared_symbols()) == set(_native.EXPORTS)
+
+
+def test_only_the_abi_is_exported(lib):
+    from paper_1409_0669_gb300 import _native
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    text_syms = {l.split()[-1] for l in out.splitlines() if l.split()[1] in ("T", "t")}
+    ours = {s for s in text_syms if not s.startswith("_")}
+    assert ours <= set(declared_symbols()) | {"_init", "_fini"}, ours - set(declared_symbols())
+
+
+def test_abi_version(lib):
+    assert lib.lak_abi_version() == 1
+
+
+def _err(lib):
+    return lib.lak_last_error().decode()
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1409_0669_gb300._native import LakCfg, LAK_EINVAL, LAK_EDTYPE, LAK_ELAYOUT, LAK_OK
+    # negative length
+    assert lib.vec_axpy(None, None, None, 1.0, -1, 0, None, None) == LAK_EINVAL
+    assert "n=-1" in _err(lib)
+    # unknown dtype
+    assert lib.vec_copy(None, None, 4, 7, None, None) == LAK_EDTYPE
+    # empty vectors are a no-op, even with NULL pointers
+    assert lib.vec_copy(None, None, 0, 0, None, None) == LAK_OK
+    assert lib.vec_axpy(None, None, None, 2.0, 0, 1, None, None) == LAK_OK
+    # bad configurations
+    for bad in (LakCfg(48, 0, 0, 0), LakCfg(1024, 0, 0, 0), LakCfg(256, -1, 0, 0),
+                LakCfg(256, 0, 3, 0), LakCfg(256, 0, 4, 2)):
+        assert lib.vec_copy(None, None, 4, 0, ctypes.byref(bad), None) == LAK_EINVAL
+    # NULL pointers with work to do
+    assert lib.vec_copy(None, None, 4, 0, None, None) == LAK_EINVAL
+    # dense_gemv: layout and leading dimension
+    assert lib.dense_gemv(None, None, None, 4, 4, 4, 5, 0, None, 0, None, None) == LAK_ELAYOUT
+    assert lib.dense_gemv(None, None, None, 4, 8, 4, 0, 0, None, 0, None, None) == LAK_EINVAL
+    assert "lda=4" in _err(lib)
+    assert lib.dense_gemv(None, None, None, 8, 4, 4, 1, 0, None, 0, None, None) == LAK_EINVAL
+    assert lib.dense_gemv(None, None, None, 0, 4, 4, 0, 0, None, 0, None, None) == LAK_OK
+    # csr_spmv: sizes
+    assert lib.csr_spmv(None, None, None, None, None, -1, 3, 0, 0, None, None) == LAK_EINVAL
+    assert lib.csr_spmv(None, None, None, None, None, 0, 3, 0, 0, None, None) == LAK_OK
+    assert lib.csr_spmv(None, None, None, None, None, 3, 3, 1 << 31, 0, None, None) == LAK_EINVAL
+    # misaligned element pointers are rejected (an FP32 element at an odd address)
+    assert lib.vec_copy(ctypes.c_void_p(0x1001), ctypes.c_void_p(0x2000), 4, 0, None,
+                        None) == LAK_EINVAL
+    # default-configuration table
+    assert lib.lak_set_default_cfg(9, 0, None) == LAK_EINVAL
+    assert lib.lak_set_default_cfg(0, 9, None) == LAK_EDTYPE
+    assert lib.lak_set_default_cfg(0, 0, ctypes.byref(LakCfg(0, 0, 0, 0))) == LAK_EINVAL
+    assert lib.lak_set_default_cfg(0, 0, ctypes.byref(LakCfg(128, 0, 4, 1))) == LAK_OK
+    assert lib.lak_set_default_cfg(0, 0, None) == LAK_OK
+
+
+def test_python_binding_imports_and_fails_loudly_without_library(tmp_path):
+    from paper_1409_0669_gb300 import _native
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        _native.load(str(tmp_path / "missing.so"))
