@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "lak.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1409_0669_gb300 import _build
-    path = _build.build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     from paper_1409_0669_gb300 import _native
     return _native.load(path)
 
