@@ -164,10 +164,10 @@ def _aligned_slices(total_elems_list, dtype, device, align_elems):
     return buf, [buf[o:o + n] for o, n in zip(offs, total_elems_list)]
 
 
-def build_sweep(device, stream_handle):
-    """Allocate and fill the sweep's inputs and return the ordered launch list."""
-    import ctypes
-
+def build_sweep(device, stream_handle, only=None):
+    """Allocate and fill the sweep's inputs and return the ordered launch list.
+    `only` (a compiled regex) keeps just the launches whose name matches, and
+    allocates nothing for the others."""
     import torch
 
     import paper_1409_0669_gb300 as lak
@@ -179,27 +179,39 @@ def build_sweep(device, stream_handle):
     sizes = synth.vector_sweep_sizes()
     gsizes = synth.gemv_sweep_sizes()
     keep = []                                   # keep tensors alive
+    def want(name):
+        return only is None or only.search(name) is not None
+
     for storage, es, seed0 in (("f32", 4, 100), ("f64", 8, 200)):
         dt = synth.torch_dtype(storage)
         code = _native.DTYPES[storage]
+        vec_names = [f"{op}_{storage}_{n}" for op in ("copy", "axpy", "dot") for n in sizes]
+        if not any(want(nm) for nm in vec_names):
+            sizes_used = []
+        else:
+            sizes_used = sizes
         # vectors: one flat buffer per role, 256-byte aligned sub-vectors
-        ybuf, ys = _aligned_slices(sizes, dt, device, 64)
-        zbuf, zs = _aligned_slices(sizes, dt, device, 64)
-        xbuf, xs = _aligned_slices(sizes, dt, device, 64)
-        synth.device_uniform_(ybuf, seed0 + 1)
-        synth.device_uniform_(zbuf, seed0 + 2)
-        xbuf.zero_()
+        if not sizes_used:
+            ybuf = zbuf = xbuf = None
+            ys = zs = xs = []
+        else:
+            ybuf, ys = _aligned_slices(sizes, dt, device, 64)
+            zbuf, zs = _aligned_slices(sizes, dt, device, 64)
+            xbuf, xs = _aligned_slices(sizes, dt, device, 64)
+            synth.device_uniform_(ybuf, seed0 + 1)
+            synth.device_uniform_(zbuf, seed0 + 2)
+            xbuf.zero_()
         outs = torch.zeros(len(sizes), dtype=dt, device=device)
         keep += [ybuf, zbuf, xbuf, outs]
-        for n, y, x in zip(sizes, ys, xs):
+        for n, y, x in zip(sizes_used, ys, xs):
             items.append(Item(f"copy_{storage}_{n}", "copy", storage, n, 2 * n * es,
                               lib.vec_copy, (x.data_ptr(), y.data_ptr(), n, code, None,
                                              stream_handle), h2d=(y,), d2h=(x,)))
-        for n, y, z, x in zip(sizes, ys, zs, xs):
+        for n, y, z, x in zip(sizes_used, ys, zs, xs):
             items.append(Item(f"axpy_{storage}_{n}", "axpy", storage, n, 3 * n * es,
                               lib.vec_axpy, (x.data_ptr(), y.data_ptr(), z.data_ptr(), 0.5, n,
                                              code, None, stream_handle), h2d=(y, z), d2h=(x,)))
-        for k, (n, y, z) in enumerate(zip(sizes, ys, zs)):
+        for k, (n, y, z) in enumerate(zip(sizes_used, ys, zs)):
             wsb = lak.vec_dot_workspace(n, storage)
             ws = torch.zeros(wsb, dtype=torch.uint8, device=device)
             keep.append(ws)
@@ -210,6 +222,8 @@ def build_sweep(device, stream_handle):
         # dense GEMV, both layouts
         for layout, lcode in (("row", 0), ("col", 1)):
             for k, n in enumerate(gsizes):
+                if not want(f"gemv_{layout}_{storage}_{n}"):
+                    continue
                 A = torch.empty(n * n, dtype=dt, device=device)
                 synth.device_normal_(A, seed0 + 10 + k + (50 if layout == "col" else 0))
                 xg = torch.empty(n, dtype=dt, device=device)
@@ -225,9 +239,13 @@ def build_sweep(device, stream_handle):
                                    code, ws.data_ptr(), ws.numel(), None, stream_handle),
                                   h2d=(A, xg), d2h=(yg,)))
         # CSR SpMV
-        for name, (rp, ci, v), ncols in (
-                ("lap3d_128", synth.laplacian_3d(128, storage), 128 ** 3),
-                ("powerlaw_2m", synth.powerlaw_csr(2_000_000, 2_000_000, 1, storage), 2_000_000)):
+        sparse = (("lap3d_128", lambda: synth.laplacian_3d(128, storage), 128 ** 3),
+                  ("powerlaw_2m", lambda: synth.powerlaw_csr(2_000_000, 2_000_000, 1, storage),
+                   2_000_000))
+        for name, make, ncols in sparse:
+            if not want(f"spmv_{name}_{storage}"):
+                continue
+            rp, ci, v = make()
             rpd, cid, vd = rp.to(device), ci.to(device), v.to(device)
             xsp = torch.empty(ncols, dtype=dt, device=device)
             synth.device_uniform_(xsp, seed0 + 40)
@@ -240,18 +258,41 @@ def build_sweep(device, stream_handle):
                               (ysp.data_ptr(), rpd.data_ptr(), cid.data_ptr(), vd.data_ptr(),
                                xsp.data_ptr(), m, ncols, nnz, code, None, stream_handle),
                               h2d=(rpd, cid, vd, xsp), d2h=(ysp,)))
+    items = [it for it in items if want(it.name)]
+    if not items:
+        raise ValueError("no launch matches the --only filter")
     return items, keep
 
 
-def run_step(items, lib_check, events=None):
+def watched_items(items):
+    """Indices of the launches timed individually: the largest size of every
+    (op, dtype) -- where the roofline is read -- and the paper's own points
+    (vectors of ~2e6 entries, the 2048^2 matrix).  Small launches run without
+    per-launch events, which would otherwise dominate their duration."""
+    best = {}
     for i, it in enumerate(items):
-        if events is not None:
-            events[i][0].record()
+        key = (it.op, it.dtype, it.name.split("_")[1] if it.op == "spmv" else "")
+        if key not in best or it.size > items[best[key]].size:
+            best[key] = i
+    idx = set(best.values())
+    for i, it in enumerate(items):
+        if it.size in (2154435, 2048):
+            idx.add(i)
+    return sorted(idx)
+
+
+def run_step(items, lib_check, events=None):
+    """One pass over every launch; `events` maps an item index to its
+    (start, end) CUDA events."""
+    for i, it in enumerate(items):
+        ev = events.get(i) if events is not None else None
+        if ev is not None:
+            ev[0].record()
         st = it.fn(*it.args)
         if st != 0:
             lib_check(it.name, st)
-        if events is not None:
-            events[i][1].record()
+        if ev is not None:
+            ev[1].record()
 
 
 # ---------------------------------------------------------------------------
@@ -390,8 +431,10 @@ def run_gb300(args):
 
     stream = torch.cuda.Stream(device=device)
     sh = stream.cuda_stream
+    import re
+    only = re.compile(args.only) if args.only else None
     with torch.cuda.stream(stream):
-        items, keep = build_sweep(device, sh)
+        items, keep = build_sweep(device, sh, only)
     torch.cuda.synchronize()
 
     def lib_check(name, st):
@@ -404,9 +447,10 @@ def run_gb300(args):
             run_step(items, lib_check)
     torch.cuda.synchronize()
 
-    # per-launch events on the launching stream, all K steps
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in items] for _ in range(K)]
+    # per-launch events on the launching stream for the watched launches, all K steps
+    watch = watched_items(items)
+    ev = [{i: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for i in watch} for _ in range(K)]
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
@@ -427,21 +471,22 @@ def run_gb300(args):
     elapsed_ms = max_over_ranks(elapsed_ms, dist, device)
 
     per = {}
-    for i, it in enumerate(items):
+    for i in watch:
+        it = items[i]
         t = sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)) / K
         per[it.name] = (it, t)
-    kernel_ms_sum = sum(t for _, t in per.values())
+    step_ms = elapsed_ms / K
 
     ms_per_step = elapsed_ms / K
     value = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
 
-    # dominant kernel: largest share of the step's kernel time
+    # dominant kernel: largest share of the step time
     dom_name, (dom_it, dom_ms) = max(per.items(), key=lambda kv: kv[1][1])
     achieved = dom_it.nbytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom_name,
-                "share": dom_ms / kernel_ms_sum, "peak_source": f"{peak_kind} hbm_gbs"}
+                "share": dom_ms / step_ms, "peak_source": f"{peak_kind} hbm_gbs"}
     if args.traffic_json and os.path.exists(args.traffic_json):
         with open(args.traffic_json) as fh:
             roofline["traffic"] = json.load(fh).get(dom_name)
@@ -469,7 +514,10 @@ def run_gb300(args):
             json.dump({"peak_gbs": peak, "rows": rows}, fh, indent=1)
 
     # end to end through the public API with host buffers (pinned), copies timed
-    e2e = run_e2e(items, keep, stream, device, max(1, min(K, args.e2e_steps)), lib_check, dist)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(items, keep, stream, device, max(1, min(K, args.e2e_steps)), lib_check,
+                      dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -479,7 +527,8 @@ def run_gb300(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "bytes_per_step": bytes_per_step,
+        "config": {"workload": WORKLOAD if not args.only else f"subset /{args.only}/ of: "
+                   + WORKLOAD, "bytes_per_step": bytes_per_step,
                    "launches_per_step": len(items),
                    "l2": "inputs larger than L2: each buffer read once per step, >1 GB of other "
                          "traffic between reuses (no explicit flush)",
@@ -552,6 +601,10 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="regex: run (and allocate) only the launches whose name matches "
+                         "(profiling captures); the result is then not the full workload")
     ap.add_argument("--sweep-json", default=None, help="write the per-size table here")
     ap.add_argument("--traffic-json", default=None,
                     help="per-kernel DRAM bytes per launch from an ncu capture")

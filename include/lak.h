@@ -13,6 +13,13 @@
  *   The library allocates nothing and frees nothing; where a kernel needs
  *   scratch memory the caller passes it in ("workspace"), sized by the matching
  *   *_workspace() query for the same arguments.
+ * Workspace layout.  Every workspace begins with a counter area of
+ *   LAK_WS_COUNTER_BYTES that must be zero-filled before the workspace is first
+ *   used; kernels touch it only with self-resetting arrival counters, so every
+ *   completed call leaves it zero again.  Scratch data follows it.  One
+ *   workspace (256-byte aligned, as large as the largest query) can therefore
+ *   serve any sequence of calls of any op and shape on one stream; calls that
+ *   share a workspace must not run concurrently on the device.
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *   default stream).  Every call is asynchronous on that stream: no call
  *   synchronises the host, and scalar results (vec_dot) stay on the device.
@@ -60,6 +67,9 @@ typedef enum {
 } lak_status;
 
 typedef enum { LAK_F32 = 0, LAK_F64 = 1, LAK_BF16 = 2, LAK_F16 = 3 } lak_dtype;
+
+/* Size of the zero-filled counter area at the start of every workspace. */
+#define LAK_WS_COUNTER_BYTES 65536
 
 typedef enum { LAK_ROW_MAJOR = 0, LAK_COL_MAJOR = 1 } lak_layout;
 
@@ -156,10 +166,8 @@ LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg)
  * to the workspace, and the last block to arrive adds the partials in FP64 in
  * block order, so the result is deterministic for a fixed configuration.
  * `out` is one device element: float for F32/BF16/F16, double for F64.
- * `workspace` (>= vec_dot_workspace() bytes, 8-byte aligned) must be
- * zero-filled before its first use; every completed call leaves its counter at
- * zero again, so it can be reused by later calls on the same stream.  Calls
- * sharing a workspace must not overlap on the device.  n = 0 writes 0.
+ * `workspace`: >= vec_dot_workspace() bytes, 256-byte aligned, laid out as
+ * described at the top of this header.  n = 0 writes 0.
  */
 LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
                            lak_dtype dtype, void *workspace, size_t ws_bytes,
@@ -185,7 +193,7 @@ LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout,
  *     the storage of a row-major matrix B (n-by-m) with layout COL_MAJOR this
  *     computes B^T x.
  * y has m elements, x has n.  `workspace` (>= dense_gemv_workspace() bytes,
- * zero-filled before first use, left reusable by every completed call) may be
+ * 256-byte aligned, laid out as described at the top of this header) may be
  * NULL when the query returns 0.  m = 0 is a no-op; n = 0 writes y = 0.
  */
 LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m,
@@ -196,9 +204,22 @@ LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m,
 /*
  * csr_spmv: y[i] = sum_{k=row_ptr[i]}^{row_ptr[i+1]-1} vals[k] * x[col_idx[k]]
  * for an m-by-n CSR matrix with nnz stored entries (textbook CSR product; the
- * paper leaves sparse formats out of its study, Sec. 1).  A group of
- * 1..32 lanes per row, sized from the mean row length nnz/m, walks the row's
- * entries and reduces with shuffles.  Requirements the library does not check
+ * paper leaves sparse formats out of its study, Sec. 1).  Three variants,
+ * chosen by the mean row length nnz/m (rounded up):
+ *   mean <= 12 (short, regular rows such as stencils): one lane per row (two
+ *     for means 9..12); the lane issues `vec` independent loads of its row at a
+ *     time through L1, so a warp keeps 32 rows in flight;
+ *   13 <= mean <= 64: warp-segmented -- a warp owns 32 consecutive rows, whose
+ *     entries are contiguous; each lane takes `vec` consecutive entries
+ *     (16-byte loads when col_idx and vals are 16-byte aligned), accumulates
+ *     them with one fused multiply-add each and splits at row ends; rows
+ *     crossing lanes are joined by a segmented warp scan, deterministically and
+ *     without atomics;
+ *   mean > 64: a power-of-two group of lanes per row (up to a warp) strides
+ *     through the row and reduces with shuffles.
+ * The environment variables LAK_SPMV_SEG_MIN_MEAN / LAK_SPMV_SEG_MAX_MEAN
+ * (read once) move the bounds of the middle range.
+ * Requirements the library does not check
  * on the device: row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[m] = nnz,
  * 0 <= col_idx[k] < n.  Repeated columns in a row are summed.  m = 0 is a
  * no-op; empty rows give 0.

@@ -1,0 +1,275 @@
+"""Autotuner for the shared launch configuration (block, grid, vec, increment).
+
+The paper's tuning space (Sec. 2) is increment type x vector length x local
+size x number of work-groups (2 x 5 x 10 x 19 = 1900 configurations).  On
+GB300 the same four axes become:
+  increment  global (grid-stride) / local (contiguous range per block)
+  vec        1, 2, 4, 8, 16 elements per thread per access group
+  block      64, 128, 256, 512 threads
+  grid       automatic (enough blocks to cover the data once) or a multiple of
+             the SM count (1, 2, 4, 8, 16, 32 blocks per SM: persistent grids)
+Each configuration is timed with CUDA events on the launching stream (median
+of `reps` launches, L2 flushed between launches when the operands fit in it).
+
+`copy_first_study` repeats the paper's central experiment (Sec. 3.2, 3.4):
+tune the copy kernel exhaustively, keep the configurations within 15 % of the
+best copy, and measure how close the best of those comes to each other
+operation's own optimum.
+
+The winners can be saved as a JSON cache keyed by GPU name and SM count and
+installed as the library's per-op defaults (lak_set_default_cfg).
+
+  python -m paper_1409_0669_gb300.autotune --op copy --storage f32 --size 100000000
+  python -m paper_1409_0669_gb300.autotune --study --storage f32 --out tune.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+from typing import Callable, Dict, List, Optional
+
+import torch
+
+from . import _native
+from ._native import DTYPES, LakCfg, LakError
+
+OPS = ("copy", "axpy", "dot", "gemv_row", "gemv_col", "spmv")
+BLOCKS = (64, 128, 256, 512)
+VECS = (1, 2, 4, 8, 16)
+GRID_PER_SM = (0, 1, 2, 4, 8, 16, 32)       # 0 = automatic
+_L2_FLUSH_BYTES = 256 << 20
+
+
+def space(sms: int) -> List[LakCfg]:
+    out = []
+    for inc in (0, 1):
+        for vec in VECS:
+            for block in BLOCKS:
+                for k in GRID_PER_SM:
+                    out.append(LakCfg(block, k * sms, vec, inc))
+    return out
+
+
+class Problem:
+    """Inputs of one op at one size on the current device, and a launcher
+    that takes a configuration (pre-marshalled C-ABI call)."""
+
+    def __init__(self, op: str, storage: str, size, device=None, seed: int = 0):
+        import synth
+        self.op, self.storage = op, storage
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream(self.device)
+        sh = self.stream.cuda_stream
+        lib = _native.load()
+        dt = synth.torch_dtype(storage)
+        es = torch.tensor([], dtype=dt).element_size()
+        code = DTYPES[storage]
+        self.keep = []
+        if op in ("copy", "axpy", "dot"):
+            n = int(size)
+            y = synth.device_uniform_(torch.empty(n, dtype=dt, device=self.device), seed + 1)
+            z = synth.device_uniform_(torch.empty(n, dtype=dt, device=self.device), seed + 2)
+            x = torch.zeros(n, dtype=dt, device=self.device)
+            out = torch.zeros(1, dtype=torch.float64 if storage == "f64" else torch.float32,
+                              device=self.device)
+            self.keep += [y, z, x, out]
+            if op == "copy":
+                self.nbytes = 2 * n * es
+                self.fn = lambda c: lib.vec_copy(x.data_ptr(), y.data_ptr(), n, code, c, sh)
+            elif op == "axpy":
+                self.nbytes = 3 * n * es
+                self.fn = lambda c: lib.vec_axpy(x.data_ptr(), y.data_ptr(), z.data_ptr(), 0.5,
+                                                 n, code, c, sh)
+            else:
+                self.nbytes = 2 * n * es
+                ws = torch.zeros(1 << 20, dtype=torch.uint8, device=self.device)
+                self.keep.append(ws)
+                self.fn = lambda c: lib.vec_dot(out.data_ptr(), y.data_ptr(), z.data_ptr(), n,
+                                                code, ws.data_ptr(), ws.numel(), c, sh)
+            self.footprint = self.nbytes
+        elif op in ("gemv_row", "gemv_col"):
+            m = n = int(size)
+            A = synth.device_normal_(torch.empty(m * n, dtype=dt, device=self.device), seed + 3)
+            xg = synth.device_uniform_(torch.empty(n, dtype=dt, device=self.device), seed + 4)
+            yg = torch.zeros(m, dtype=dt, device=self.device)
+            ws = torch.zeros(512 << 20, dtype=torch.uint8, device=self.device)
+            self.keep += [A, xg, yg, ws]
+            lay = 0 if op == "gemv_row" else 1
+            self.nbytes = (m * n + m + n) * es
+            self.fn = lambda c: lib.dense_gemv(yg.data_ptr(), A.data_ptr(), xg.data_ptr(), m, n,
+                                               n if lay == 0 else m, lay, code, ws.data_ptr(),
+                                               ws.numel(), c, sh)
+            self.footprint = self.nbytes
+        elif op == "spmv":
+            if size == "lap3d_128":
+                rp, ci, v = synth.laplacian_3d(128, storage)
+                ncols = 128 ** 3
+            elif size == "lap2d_256":
+                rp, ci, v = synth.laplacian_2d(256, storage)
+                ncols = 256 ** 2
+            elif size == "powerlaw_2m":
+                rp, ci, v = synth.powerlaw_csr(2_000_000, 2_000_000, 1, storage)
+                ncols = 2_000_000
+            else:
+                raise ValueError(f"unknown sparse matrix {size!r}")
+            rpd, cid, vd = rp.to(self.device), ci.to(self.device), v.to(self.device)
+            xs = synth.device_uniform_(torch.empty(ncols, dtype=dt, device=self.device), seed + 5)
+            m = rp.numel() - 1
+            nnz = v.numel()
+            ys = torch.zeros(m, dtype=dt, device=self.device)
+            self.keep += [rpd, cid, vd, xs, ys]
+            self.nbytes = nnz * (es + 4) + (m + 1) * 4 + ncols * es + m * es
+            self.fn = lambda c: lib.csr_spmv(ys.data_ptr(), rpd.data_ptr(), cid.data_ptr(),
+                                             vd.data_ptr(), xs.data_ptr(), m, ncols, nnz, code,
+                                             c, sh)
+            self.footprint = self.nbytes
+        else:
+            raise ValueError(op)
+        l2 = torch.cuda.get_device_properties(self.device).L2_cache_size
+        self.flush = torch.empty(_L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.device) \
+            if self.footprint < 2 * l2 else None
+
+    def time_cfg(self, cfg: Optional[LakCfg], reps: int = 10, warm: int = 2) -> float:
+        """Median launch time in microseconds (raises LakError on a bad cfg)."""
+        import ctypes
+        cptr = ctypes.byref(cfg) if cfg is not None else None
+        for _ in range(warm):
+            st = self.fn(cptr)
+            _native.check(self.op, st)
+        times = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(reps):
+            if self.flush is not None:
+                self.flush.zero_()
+            ev0.record(self.stream)
+            st = self.fn(cptr)
+            ev1.record(self.stream)
+            _native.check(self.op, st)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) * 1e3)
+        return statistics.median(times)
+
+
+def tune(op: str, storage: str, size, reps: int = 10, cfgs: Optional[List[LakCfg]] = None,
+         problem: Optional[Problem] = None) -> List[Dict]:
+    """Time every configuration; results sorted fastest first."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    prob = problem or Problem(op, storage, size, dev)
+    results = []
+    for c in (cfgs if cfgs is not None else space(sms)):
+        try:
+            us = prob.time_cfg(c, reps)
+        except LakError:
+            continue
+        results.append({"cfg": list(c.as_tuple()), "us": us,
+                        "GBs": prob.nbytes / (us * 1e-6) / 1e9})
+    results.sort(key=lambda r: r["us"])
+    return results
+
+
+def copy_first_study(storage: str, sizes: Dict[str, object], keep_frac: float = 0.85,
+                     reps: int = 10) -> Dict:
+    """Sec. 3.2 / 3.4 on GB300: configurations within (1 - keep_frac) of the
+    best copy, evaluated on the other ops, against each op's own best."""
+    copy = tune("copy", storage, sizes["copy"], reps)
+    best = copy[0]["GBs"]
+    cands = [r for r in copy if r["GBs"] >= keep_frac * best]
+    report = {"storage": storage, "copy_best_GBs": best, "candidates": len(cands),
+              "space": len(copy), "ops": {}}
+    cand_cfgs = [LakCfg(*r["cfg"]) for r in cands]
+    per_op = {}
+    for op in ("axpy", "dot", "gemv_row", "gemv_col", "spmv"):
+        own = tune(op, storage, sizes[op], reps)
+        prob = Problem(op, storage, sizes[op])
+        from_copy = tune(op, storage, sizes[op], reps, cand_cfgs, prob)
+        per_op[op] = {r_cfg: r for r_cfg, r in ((tuple(r["cfg"]), r) for r in from_copy)}
+        report["ops"][op] = {
+            "own_best": own[0], "best_from_copy": from_copy[0] if from_copy else None,
+            "ratio": (from_copy[0]["GBs"] / own[0]["GBs"]) if from_copy and own else None,
+            "default": _default_point(prob, reps)}
+    # one shared configuration: the copy candidate with the best worst-case ratio
+    shared, shared_score = None, -1.0
+    for c in cands:
+        key = tuple(c["cfg"])
+        ratios = []
+        for op, table in per_op.items():
+            r = table.get(key)
+            if r is None:
+                break
+            ratios.append(r["GBs"] / report["ops"][op]["own_best"]["GBs"])
+        else:
+            if min(ratios) > shared_score:
+                shared, shared_score = key, min(ratios)
+    report["shared_cfg"] = list(shared) if shared else None
+    report["shared_worst_ratio"] = shared_score if shared else None
+    report["copy_top"] = copy[:10]
+    return report
+
+
+def _default_point(prob: Problem, reps: int) -> Dict:
+    us = prob.time_cfg(None, reps)
+    return {"us": us, "GBs": prob.nbytes / (us * 1e-6) / 1e9}
+
+
+def cache_key() -> str:
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|sms={p.multi_processor_count}"
+
+
+def save_cache(path: str, entries: Dict[str, List[int]]):
+    """entries: {"<op>:<storage>": [block, grid, vec, increment]}"""
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        data = {}
+    data.setdefault(cache_key(), {}).update(entries)
+    with open(path, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+
+
+def apply_cache(path: str) -> int:
+    """Install the cached configurations for this GPU as library defaults."""
+    from . import set_default_cfg
+    with open(path) as fh:
+        data = json.load(fh)
+    entries = data.get(cache_key(), {})
+    for key, cfg in entries.items():
+        op, storage = key.split(":")
+        set_default_cfg(op, storage, tuple(cfg))
+    return len(entries)
+
+
+def _main(argv=None):
+    ap = argparse.ArgumentParser(description="launch-configuration autotuner")
+    ap.add_argument("--op", choices=OPS)
+    ap.add_argument("--storage", default="f32", choices=list(DTYPES))
+    ap.add_argument("--size", default="100000000")
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--top", type=int, default=15)
+    ap.add_argument("--study", action="store_true", help="copy-first transfer study")
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    size = args.size
+    if size.isdigit():
+        size = int(size)
+    if args.study:
+        sizes = {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
+                 "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"}
+        rep = copy_first_study(args.storage, sizes, reps=args.reps)
+        text = json.dumps(rep, indent=1)
+    else:
+        res = tune(args.op, args.storage, size, args.reps)
+        text = json.dumps({"op": args.op, "storage": args.storage, "size": size,
+                           "top": res[:args.top], "worst": res[-3:], "count": len(res)}, indent=1)
+    print(text)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(text)
+
+
+if __name__ == "__main__":
+    _main()

@@ -197,12 +197,10 @@ lak_status gemv_col_t(void *y, const void *A, const void *x, int64_t m, int64_t 
     const T *xp = static_cast<const T *>(x);
     const int64_t tiles = ceil_div(m, 32LL * L.vec);
     const int64_t cps = splits > 1 ? ceil_div(n, splits) : (n > 0 ? n : 1);
-    unsigned int *tickets = static_cast<unsigned int *>(ws);
+    unsigned int *tickets = static_cast<unsigned int *>(ws);     // counter area
     Ac *partials = nullptr;
-    if (splits > 1) {
-        const size_t tbytes = (size_t)((tiles * 4 + 255) / 256 * 256);
-        partials = reinterpret_cast<Ac *>(static_cast<char *>(ws) + tbytes);
-    }
+    if (splits > 1)
+        partials = reinterpret_cast<Ac *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const dim3 grid((unsigned)tiles, (unsigned)splits);
     const size_t smem = (size_t)(L.block / 32) * 32 * L.vec * sizeof(Ac);
 #define LAK_COL(VV)                                                                          \

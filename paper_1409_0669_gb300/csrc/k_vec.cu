@@ -217,7 +217,7 @@ lak_status dot_t(int vec, void *out, const void *x, const void *y, int64_t n, in
     const T *xp = static_cast<const T *>(x);
     const T *yp = static_cast<const T *>(y);
     unsigned int *counter = static_cast<unsigned int *>(ws);
-    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 8);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const int64_t nchunks = (n - head) / vec;
 #define LAK_DOT(VV)                                                                     \
     dot_kernel<T, VV><<<L.grid, L.block, 0, s>>>(out, xp, yp, n, head, nchunks, L.inc, \

@@ -3,6 +3,7 @@
 // dispatch to the kernel launchers.  Host code only.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "lak_internal.cuh"
@@ -76,22 +77,47 @@ const DeviceInfo *device_info() {
 
 namespace {
 
-// Built-in defaults per op: the paper's GPU guideline (Sec. 4: 128 or 256
-// work items per group, many groups, global increment on GPUs), with the
-// per-thread vector width set to the widest single load for the storage type.
-lak_cfg builtin_default(lak_op op, lak_dtype dt) {
-    const int es = esize(dt);
-    lak_cfg c{256, 0, 0, LAK_INC_GLOBAL};
+// Built-in defaults per op, measured on GB300 with the autotuner (every
+// combination of block 64..512, grid 1..32 blocks per SM or automatic, vec
+// 1..16 and both increments, at the largest sweep size).  Like the paper's GPU
+// guideline (Sec. 4) they favour many work-groups and the global increment;
+// unlike it, wide per-thread accesses pay off on GB300 (32-64 bytes in flight
+// per thread).  `bytes` is the per-thread access width, turned into a vector
+// length for the storage type; the grid is stored per SM.
+struct DefaultCfg {
+    int block, grid_per_sm, bytes, inc;
+};
+
+DefaultCfg default_row(lak_op op, lak_dtype dt) {
     switch (op) {
     case LAK_OP_COPY:
-    case LAK_OP_AXPY:
-    case LAK_OP_DOT: c.vec = 32 / es; break;           // one 256-bit access
-    case LAK_OP_GEMV_ROW: c.vec = 16 / es; break;      // one 128-bit access
-    case LAK_OP_GEMV_COL: c.vec = 16 / es; break;
-    case LAK_OP_SPMV: c.vec = 2; break;
-    default: break;
+    case LAK_OP_AXPY: return {512, 32, 64, LAK_INC_GLOBAL};
+    case LAK_OP_DOT: return {512, dt == LAK_F64 ? 4 : 8, dt == LAK_F64 ? 32 : 16, LAK_INC_GLOBAL};
+    case LAK_OP_GEMV_ROW: return {128, 0, dt == LAK_F64 ? 16 : 32, LAK_INC_GLOBAL};
+    case LAK_OP_GEMV_COL: return {512, 0, 32, LAK_INC_LOCAL};
+    case LAK_OP_SPMV: return {256, 0, 0, LAK_INC_GLOBAL};
+    default: return {256, 0, 16, LAK_INC_GLOBAL};
     }
+}
+
+int vec_for_bytes(int bytes, int es) {
+    int v = bytes / es;
+    if (v < 1) v = 1;
+    if (v > 16) v = 16;
+    return v;
+}
+
+lak_cfg builtin_default(lak_op op, lak_dtype dt) {
+    const DefaultCfg d = default_row(op, dt);
+    lak_cfg c{d.block, 0, 0, d.inc};
+    c.vec = op == LAK_OP_SPMV ? 8 : vec_for_bytes(d.bytes, esize(dt));
     return c;
+}
+
+// Automatic grid cap (blocks per SM) for the grid-stride vector kernels.
+int default_grid_per_sm(lak_op op, lak_dtype dt) {
+    const int g = default_row(op, dt).grid_per_sm;
+    return g > 0 ? g : 0;
 }
 
 lak_cfg g_override[LAK_OP_COUNT][4];
@@ -157,7 +183,8 @@ lak_status plan_vector(lak_op op, lak_dtype dt, int64_t n, const lak_cfg *cfg,
     int64_t grid = c.grid;
     if (grid == 0) {
         const int64_t need = ceil_div(nchunks > 0 ? nchunks : 1, c.block);
-        const int64_t cap = waves_grid(di, c.block);
+        const int per_sm = default_grid_per_sm(op, dt);
+        const int64_t cap = per_sm > 0 ? (int64_t)per_sm * di->sms : waves_grid(di, c.block);
         grid = need < cap ? need : cap;
     }
     if (grid < 1) grid = 1;
@@ -228,12 +255,12 @@ lak_status plan_gemv_col(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const 
     const int64_t max_splits = n / (4LL * nwarps);      // >= 4 columns per warp per split
     if (splits > max_splits) splits = max_splits;
     if (splits > 65535) splits = 65535;
+    // one arrival counter per row tile, all inside the workspace counter area
+    if (tiles > LAK_WS_COUNTER_BYTES / 4) splits = 1;
     if (splits < 1) splits = 1;
     const int acc_bytes = dt == LAK_F64 ? 8 : 4;
     size_t ws = 0;
-    if (splits > 1) {
-        ws = (size_t)((tiles * 4 + 255) / 256 * 256) + (size_t)splits * (size_t)m * acc_bytes;
-    }
+    if (splits > 1) ws = (size_t)LAK_WS_COUNTER_BYTES + (size_t)splits * (size_t)m * acc_bytes;
     out->L = Launch{c.block, (int)(tiles * splits > 0x7fffffff ? 0x7fffffff : tiles * splits), vec,
                     c.increment};
     out->splits = (int)splits;
@@ -244,8 +271,30 @@ lak_status plan_gemv_col(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const 
 
 struct SpmvPlan {
     Launch L;
-    int group;
+    int group;     // lanes per row (long-row variant); 0 = warp-stream variant
 };
+
+// Mean row lengths between which the warp-segmented variant is used; below
+// the range one lane (or two) per row, above it a group of lanes per row.
+int64_t env_int(const char *name, int64_t dflt) {
+    const char *e = getenv(name);
+    if (e && *e) {
+        char *end = nullptr;
+        const long long x = strtoll(e, &end, 10);
+        if (end && *end == 0 && x >= 0) return (int64_t)x;
+    }
+    return dflt;
+}
+
+int64_t spmv_seg_min_mean() {
+    static const int64_t v = env_int("LAK_SPMV_SEG_MIN_MEAN", 13);
+    return v;
+}
+
+int64_t spmv_seg_max_mean() {
+    static const int64_t v = env_int("LAK_SPMV_SEG_MAX_MEAN", 64);
+    return v;
+}
 
 lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, SpmvPlan *out) {
     const DeviceInfo *di = device_info();
@@ -253,15 +302,21 @@ lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, S
     lak_cfg c = base_cfg(LAK_OP_SPMV, dt, cfg);
     int vec = c.vec ? c.vec : builtin_default(LAK_OP_SPMV, dt).vec;
     const int64_t mean = m > 0 ? ceil_div(nnz, m) : 1;
-    // lanes per row: the power of two covering the mean row length in `vec`
-    // loads per lane, between 1 and a warp
-    int G = 1;
-    while (G < 32 && (int64_t)G * vec < mean) G *= 2;
-    const int bp = block_pow2(c.block);
-    if (G > bp) G = bp;
-    const int R = c.block / G;
+    int G = 0;
+    int64_t rows_per_block;
+    if (mean >= spmv_seg_min_mean() && mean <= spmv_seg_max_mean()) {
+        rows_per_block = c.block;                // a warp per 32 rows
+    } else {
+        // lanes per row: the power of two covering the mean row length in
+        // `vec` loads per lane, up to a warp
+        G = 1;
+        while (G < 32 && (int64_t)G * vec < mean) G *= 2;
+        const int bp = block_pow2(c.block);
+        if (G > bp) G = bp;
+        rows_per_block = c.block / G;
+    }
     int64_t grid = c.grid;
-    if (grid == 0) grid = ceil_div(m > 0 ? m : 1, R);
+    if (grid == 0) grid = ceil_div(m > 0 ? m : 1, rows_per_block);
     if (grid > 0x7fffffff) grid = 0x7fffffff;
     out->L = Launch{c.block, (int)grid, vec, c.increment};
     out->group = G;
@@ -417,7 +472,7 @@ LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg)
     c.vec = 1;
     if (plan_vector(LAK_OP_DOT, dtype, n, &c, nullptr, 0, &p1) != LAK_OK) return 0;
     const int grid = p1.L.grid > p.L.grid ? p1.L.grid : p.L.grid;
-    return 8 + 8 * (size_t)grid;
+    return (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)grid;
 }
 
 LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n, lak_dtype dtype,
@@ -442,11 +497,12 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n, l
     VecPlan p;
     st = plan_vector(LAK_OP_DOT, dtype, n, cfg, ptrs, 2, &p);
     if (st != LAK_OK) return st;
-    const size_t need = 8 + 8 * (size_t)p.L.grid;
+    const size_t need = (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)p.L.grid;
     if (!workspace || ws_bytes < need)
         return fail(LAK_EWORKSPACE, "vec_dot: workspace of %zu bytes needed, %zu given", need,
                     workspace ? ws_bytes : (size_t)0);
-    if ((uintptr_t)workspace % 8) return fail(LAK_EWORKSPACE, "vec_dot: workspace not 8-byte aligned");
+    if ((uintptr_t)workspace % 256)
+        return fail(LAK_EWORKSPACE, "vec_dot: workspace not 256-byte aligned");
     return launch_dot(dtype, out, x, y, n, workspace, p.L, p.head, s);
 }
 

@@ -6,9 +6,13 @@ Bars (stated for these kernels):
                                 a single rounding on both sides)
   FP32 dot / GEMV / SpMV ...... norm-wise relative error <= 1e-5
   FP64 (all) .................. <= 1e-12
-  BF16 / FP16 storage ......... outputs within 1 ulp of the storage type of the
-                                oracle on the same (quantised) inputs; dot
-                                (FP32 output) norm-wise <= 1e-5
+  BF16 / FP16 storage ......... element-wise: one ulp of the storage type at
+                                the oracle's value (output rounding) plus the
+                                worst-case FP32 summation error n * 2^-24 *
+                                sum_j |a_ij x_j| for a row of n terms; and
+                                norm-wise within one unit roundoff of the
+                                storage type.  Dot (FP32 output): norm-wise
+                                <= 1e-5 as for FP32
 """
 from __future__ import annotations
 
@@ -74,3 +78,20 @@ def assert_canary(buf: torch.Tensor, n: int, pad: int = 64):
     b = buf.detach().cpu()
     assert torch.isnan(b[:pad].float()).all() and torch.isnan(b[pad + n:].float()).all(), \
         "a kernel wrote outside its output"
+
+
+UNIT_ROUNDOFF = {"f32": 2.0 ** -24, "f64": 2.0 ** -53, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}
+
+
+def assert_reduced_sum(got: np.ndarray, ref: np.ndarray, abs_terms: np.ndarray,
+                       nterms: np.ndarray, storage: str, what=""):
+    """Outputs of an FP32-accumulated sum stored in BF16/FP16 (see module doc)."""
+    ref_r = oracle.round_to(ref, storage)
+    bound = spacing(ref_r, storage) + nterms * 2.0 ** -24 * abs_terms
+    bad = np.nonzero(np.abs(got - ref_r) > bound)[0]
+    assert bad.size == 0, (f"{what}: {bad.size} elements beyond the bound; first at {bad[:5]}: "
+                           f"got {got[bad[:5]]}, ref {ref_r[bad[:5]]}")
+    nref = np.linalg.norm(ref)
+    if nref > 0:
+        err = np.linalg.norm(got - ref) / nref
+        assert err <= 2 * UNIT_ROUNDOFF[storage], f"{what}: norm-wise {err:.3e}"

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from checks import assert_canary, assert_normwise, assert_ulp, canary_buffer, host
+from checks import assert_canary, assert_normwise, assert_reduced_sum, canary_buffer, host
 
 pytestmark = pytest.mark.gpu
 
@@ -36,12 +36,15 @@ def make_matrix(m, n, layout, storage, pad, seed):
     return buf.reshape(-1).cuda(), lda, vals
 
 
-def check(got_t, ref64, storage, what):
+def check(got_t, ref64, storage, what, A=None, x=None, m=0, n=0, lda=0, layout="row"):
     got = host(got_t)
     if storage in ("f32", "f64"):
         assert_normwise(got, ref64, storage, what)
     else:
-        assert_ulp(got, oracle.round_to(ref64, storage), storage, 1.0, what)
+        absA = np.abs(oracle.widen(A.cpu()))
+        abs_terms = oracle.gemv(np.nan_to_num(absA), np.abs(oracle.widen(x.cpu())), m, n, lda,
+                                layout)
+        assert_reduced_sum(got, ref64, abs_terms, np.full(m, n), storage, what)
 
 
 @pytest.mark.parametrize("storage", STORAGES)
@@ -56,7 +59,7 @@ def test_gemv(storage, layout, shape, pad):
     lak().dense_gemv(A, x, y=y, m=m, n=n, lda=lda, layout=layout)
     torch.cuda.synchronize()
     ref = oracle.gemv(A.cpu(), x.cpu(), m, n, lda, layout)
-    check(y, ref, storage, f"gemv {layout} {shape} lda={lda}")
+    check(y, ref, storage, f"gemv {layout} {shape} lda={lda}", A, x, m, n, lda, layout)
     assert_canary(buf, m)
 
 

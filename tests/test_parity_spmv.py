@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from checks import assert_canary, assert_normwise, assert_ulp, canary_buffer, host
+from checks import assert_canary, assert_normwise, assert_reduced_sum, canary_buffer, host
 
 pytestmark = pytest.mark.gpu
 
@@ -23,12 +23,14 @@ def run(rp, ci, v, x, cfg=None, y=None):
     return lak().csr_spmv(rp.cuda(), ci.cuda(), v.cuda(), x.cuda(), y=y, cfg=cfg)
 
 
-def check(y_t, ref, storage, what):
+def check(y_t, ref, storage, what, rp=None, ci=None, v=None, x=None):
     got = host(y_t)
     if storage in ("f32", "f64"):
         assert_normwise(got, ref, storage, what)
     else:
-        assert_ulp(got, oracle.round_to(ref, storage), storage, 1.0, what)
+        abs_terms = oracle.csr_spmv(rp, ci, np.abs(oracle.widen(v)), np.abs(oracle.widen(x)))
+        nterms = np.diff(rp.numpy()).astype(np.float64)
+        assert_reduced_sum(got, ref, abs_terms, nterms, storage, what)
 
 
 def matrices(storage):
@@ -38,6 +40,8 @@ def matrices(storage):
     yield "powerlaw_20k", synth.powerlaw_csr(20_000, 20_000, 1, storage), 20_000
     yield "random_empty_dup", synth.random_csr(5003, 4001, 2, storage, 0, 40, 0.3, True), 4001
     yield "single_row", synth.random_csr(1, 3000, 3, storage, 2000, 2000), 3000
+    yield "long_rows", synth.random_csr(700, 5000, 7, storage, 100, 400), 5000     # vector variant
+    yield "batch_like", synth.random_csr(3000, 3000, 8, storage, 5, 64), 3000
     yield "all_empty", synth.random_csr(77, 10, 4, storage, 0, 0), 10
 
 
@@ -51,7 +55,7 @@ def test_spmv(storage, cfg):
         run(rp, ci, v, x, cfg, y=y)
         torch.cuda.synchronize()
         ref = oracle.csr_spmv(rp, ci, v, x)
-        check(y, ref, storage, f"{name} cfg={cfg}")
+        check(y, ref, storage, f"{name} cfg={cfg}", rp, ci, v, x)
         assert_canary(buf, rp.numel() - 1)
 
 
