@@ -174,6 +174,31 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
                            const lak_cfg *cfg, void *stream);
 
 /*
+ * vec_dot_noalloc: the same inner product as vec_dot (same kernel, result and
+ * tolerance), for callers that cannot give the library scratch memory -- for
+ * instance a host application whose own memory manager owns every device
+ * buffer and hands out only the operands, or a binding from another language
+ * that has no device allocator at hand.  The paper has no counterpart; this is
+ * an interface convenience of this library.
+ *   Scratch: a fixed array of LAK_WS_COUNTER_BYTES + 8 * LAK_DOT_NOALLOC_MAX_BLOCKS
+ *     bytes (about 128 KiB) compiled into the library; every GPU that loads the
+ *     library holds it until the process exits.  The call allocates nothing.
+ *   Limit: the launch may use at most LAK_DOT_NOALLOC_MAX_BLOCKS blocks (one
+ *     partial sum each); a configuration asking for more is rejected with
+ *     LAK_EINVAL and launches nothing.  Default configurations stay far below.
+ *   First call per device: looks up the array's device address (and may load
+ *     the library's GPU code onto the device); make it before any stream
+ *     capture starts.
+ *   Sharing: all calls on a device use the same array.  Calls that overlap on
+ *     the GPU (e.g. on different streams) race and give wrong results; each call
+ *     clears the arrival counter before its kernel runs.
+ * Arguments as for vec_dot, without the workspace.  n = 0 writes 0.
+ */
+#define LAK_DOT_NOALLOC_MAX_BLOCKS 8192
+LAK_API lak_status vec_dot_noalloc(void *out, const void *x, const void *y, int64_t n,
+                                   lak_dtype dtype, const lak_cfg *cfg, void *stream);
+
+/*
  * Workspace bytes dense_gemv needs (column-major split-K partials and per-tile
  * counters; 0 for row-major) on the current device.
  */

@@ -23,7 +23,7 @@ import torch
 from . import _native
 from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
-__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "dense_gemv",
+__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "resolve_cfg", "set_default_cfg", "Cfg",
            "LakError", "storage_of", "library_path"]
 
@@ -179,6 +179,26 @@ def vec_dot(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None
                       _dev_ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                       _cfg_ptr(cfg), sh)
     _native.check("vec_dot", st)
+    return out
+
+
+def vec_dot_noalloc(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """<x, y> like vec_dot, but using the library's built-in scratch instead of a
+    workspace (for callers that cannot provide device scratch memory; calls
+    must not overlap on the GPU -- see include/lak.h)."""
+    s = _same_storage(x, y)
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    odt = torch.float64 if s == "f64" else torch.float32
+    if out is None:
+        out = torch.empty(1, dtype=odt, device=x.device)
+    elif out.dtype != odt or out.numel() < 1:
+        raise TypeError(f"out must be a {odt} tensor with at least one element")
+    st = _lib.vec_dot_noalloc(_dev_ptr(out, "out"), _vec_arg(x, "x"), _vec_arg(y, "y"), n,
+                              DTYPES[s], _cfg_ptr(cfg), _stream(stream))
+    _native.check("vec_dot_noalloc", st)
     return out
 
 

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_PKG, "liblak_gb300.so")
 
 # enums of lak.h
 LAK_OK, LAK_EINVAL, LAK_EDTYPE, LAK_ELAYOUT, LAK_ECUDA, LAK_EWORKSPACE = 0, -1, -2, -3, -4, -5
+DOT_NOALLOC_MAX_BLOCKS = 8192          # LAK_DOT_NOALLOC_MAX_BLOCKS
 STATUS_NAMES = {0: "LAK_OK", -1: "LAK_EINVAL", -2: "LAK_EDTYPE", -3: "LAK_ELAYOUT",
                 -4: "LAK_ECUDA", -5: "LAK_EWORKSPACE"}
 DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
@@ -22,8 +23,8 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 
 # exported symbols, in header order (checked by the ABI test)
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
-           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "dense_gemv_workspace",
-           "dense_gemv", "csr_spmv")
+           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_noalloc",
+           "dense_gemv_workspace", "dense_gemv", "csr_spmv")
 
 
 class LakCfg(ctypes.Structure):
@@ -59,6 +60,7 @@ _SIGNATURES = {
     "vec_axpy": (_I32, [_P, _P, _P, ctypes.c_double, _I64, _I32, _CFGP, _P]),
     "vec_dot_workspace": (_SZ, [_I64, _I32, _CFGP]),
     "vec_dot": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
+    "vec_dot_noalloc": (_I32, [_P, _P, _P, _I64, _I32, _CFGP, _P]),
     "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
     "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
     "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
