@@ -418,6 +418,64 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def fp64_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """FP64 FMA roof of GB300: 2 FP64 FMA (4 flop) per SM per clock -- the unit
+    count that gives the nominal 1.25 TFLOP/s at 152 SMs and 2.07 GHz."""
+    return sms * 4.0 * sm_mhz * 1e6 / 1e12
+
+
+def flops_of(it) -> float:
+    """Algorithmic floating-point operations of one launch (FMA = 2)."""
+    if it.op == "axpy":
+        return 2.0 * it.size
+    if it.op == "dot":
+        return 2.0 * it.size
+    if it.op.startswith("gemv"):
+        return 2.0 * it.size * it.size
+    if it.op == "spmv":
+        es = 8 if it.dtype == "f64" else 4
+        m = it.size
+        # nbytes = nnz*(es+4) + (m+1)*4 + n*es + m*es with n = m for these matrices
+        nnz = (it.nbytes - (m + 1) * 4 - 2 * m * es) / (es + 4)
+        return 2.0 * nnz
+    return 0.0
+
+
+def roofline_of(it, ms, hbm_peak, hbm_kind, fp64_peak):
+    """The binding roof of one launch: HBM, or the FP64 FMA pipe for FP64
+    kernels whose FP64 fraction is the larger one."""
+    gbs = it.nbytes / (ms * 1e-3) / 1e9
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+           "frac": gbs / hbm_peak, "peak_source": f"{hbm_kind} hbm_gbs (copy)"}
+    if it.dtype != "f64":
+        return hbm, None
+    tf = flops_of(it) / (ms * 1e-3) / 1e12
+    alu = {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+           "frac": tf / fp64_peak,
+           "peak_source": "derived: SMs x 4 FP64 flop/clk x median SM clock under load"}
+    return (alu, hbm) if alu["frac"] > hbm["frac"] else (hbm, alu)
+
+
+def recorded_traffic(path, name):
+    """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
+    when there is no record or the kernel's source changed since the capture."""
+    import hashlib
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh).get(name)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        with open(src, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != rec["sha256"]:
+                return None
+    except OSError:
+        return None
+    return rec["dram_bytes"]
+
+
 def run_gb300(args):
     import torch
 
@@ -482,23 +540,31 @@ def run_gb300(args):
     peak, peak_kind = load_peaks()
 
     # dominant kernel: largest share of the step time
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = fp64_peak_tflops(sms, sm_mhz)
     dom_name, (dom_it, dom_ms) = max(per.items(), key=lambda kv: kv[1][1])
-    achieved = dom_it.nbytes / (dom_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom_name,
-                "share": dom_ms / step_ms, "peak_source": f"{peak_kind} hbm_gbs"}
-    if args.traffic_json and os.path.exists(args.traffic_json):
-        with open(args.traffic_json) as fh:
-            roofline["traffic"] = json.load(fh).get(dom_name)
+    bind, other = roofline_of(dom_it, dom_ms, peak, peak_kind, fp64_peak)
+    roofline = dict(bind)
+    roofline.update({"traffic": None, "kernel": dom_name, "share": dom_ms / step_ms,
+                     "bytes_per_launch": dom_it.nbytes, "flops_per_launch": flops_of(dom_it),
+                     "ms_per_launch": dom_ms})
+    if other is not None:
+        roofline["other"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    roofline["traffic"] = recorded_traffic(args.traffic_json, dom_name)
 
     # per (op, dtype) summary at the largest size, and the paper's points
     summary = {}
     for name, (it, t) in per.items():
-        key = f"{it.op}_{it.dtype}"
+        if it.size in (2154435, 2048):
+            continue
+        key = f"{it.op}_{name.split('_')[1]}_{it.dtype}" if it.op == "spmv" else \
+            f"{it.op}_{it.dtype}"
         gbs = it.nbytes / (t * 1e-3) / 1e9
-        if key not in summary or it.size >= summary[key]["size"]:
-            summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac": round(gbs / peak, 4),
-                            "us": round(t * 1e3, 2)}
+        b, _ = roofline_of(it, t, peak, peak_kind, fp64_peak)
+        summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
+                        "us": round(t * 1e3, 2), "bound": b["bound"],
+                        "frac_bound": round(b["frac"], 4)}
     for name in ("copy_f64_2154435", "axpy_f64_2154435", "dot_f64_2154435",
                  "gemv_row_f64_2048"):
         if name in per:
@@ -606,8 +672,8 @@ def main(argv=None):
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")
     ap.add_argument("--sweep-json", default=None, help="write the per-size table here")
-    ap.add_argument("--traffic-json", default=None,
-                    help="per-kernel DRAM bytes per launch from an ncu capture")
+    ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "dram_traffic.json"),
+                    help="per-kernel DRAM bytes per launch recorded from an ncu capture")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

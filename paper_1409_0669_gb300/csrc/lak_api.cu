@@ -95,7 +95,7 @@ DefaultCfg default_row(lak_op op, lak_dtype dt) {
     case LAK_OP_DOT: return {512, dt == LAK_F64 ? 4 : 8, dt == LAK_F64 ? 32 : 16, LAK_INC_GLOBAL};
     case LAK_OP_GEMV_ROW: return {128, 0, dt == LAK_F64 ? 16 : 32, LAK_INC_GLOBAL};
     case LAK_OP_GEMV_COL: return {512, 0, 32, LAK_INC_LOCAL};
-    case LAK_OP_SPMV: return {256, 0, 0, LAK_INC_GLOBAL};
+    case LAK_OP_SPMV: return {64, 0, 0, LAK_INC_GLOBAL};
     default: return {256, 0, 16, LAK_INC_GLOBAL};
     }
 }
@@ -110,7 +110,7 @@ int vec_for_bytes(int bytes, int es) {
 lak_cfg builtin_default(lak_op op, lak_dtype dt) {
     const DefaultCfg d = default_row(op, dt);
     lak_cfg c{d.block, 0, 0, d.inc};
-    c.vec = op == LAK_OP_SPMV ? 8 : vec_for_bytes(d.bytes, esize(dt));
+    c.vec = op == LAK_OP_SPMV ? 4 : vec_for_bytes(d.bytes, esize(dt));
     return c;
 }
 
