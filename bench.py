@@ -476,6 +476,147 @@ def recorded_traffic(path, name):
     return rec["dram_bytes"]
 
 
+def _median_ms(fn, reps, flush=None):
+    """Median CUDA-event time of `fn`; `flush` (a buffer larger than L2) is read
+    before each launch, which evicts L2 without leaving dirty lines behind."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.sum()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_precision(device, reps=20):
+    """The same data stored in FP32, BF16 and FP16 (FP32 arithmetic): time of
+    every kernel relative to FP32, and its error against the FP64 oracle on the
+    ORIGINAL FP32 data (quantisation included); plus the compensated inner
+    product on 1e8 mixed-sign values of magnitude 1e-4..1e4.  L2 is flushed
+    (a 256 MB buffer read) before every timed launch."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1409_0669_gb300 as lak
+    import synth
+
+    oracle.build()
+    dev = device
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    n = 100_000_000
+    g = 16384
+    y32 = synth.device_uniform_(torch.empty(n, device=dev), 901)
+    z32 = synth.device_uniform_(torch.empty(n, device=dev), 902)
+    A32 = synth.device_normal_(torch.empty(g * g, device=dev), 903)
+    xg32 = synth.device_uniform_(torch.empty(g, device=dev), 904)
+    lap = synth.laplacian_3d(128, "f32")
+    pl = synth.powerlaw_csr(2_000_000, 2_000_000, 1, "f32")
+    xl32 = synth.device_uniform_(torch.empty(128 ** 3, device=dev), 905)
+    xp32 = synth.device_uniform_(torch.empty(2_000_000, device=dev), 906)
+
+    # FP64 oracle references on the original FP32 data
+    rng = synth.rng(907)
+    idx = np.sort(rng.choice(n, 1_000_000, replace=False))
+    yh, zh = y32.cpu(), z32.cpu()
+    ref = {"axpy": oracle.axpy(yh.numpy()[idx], zh.numpy()[idx], 0.5),
+           "dot": oracle.dot(yh, zh)}
+    dot_scale = float(np.linalg.norm(yh.double().numpy()) * np.linalg.norm(zh.double().numpy()))
+    del yh, zh
+    rows = np.sort(rng.choice(g, 96, replace=False))
+    Ah, xgh = A32.cpu(), xg32.cpu()
+    ref["gemv_row"] = oracle.gemv_entries(Ah, xgh, rows, g, g, "row")
+    ref["gemv_col"] = oracle.gemv_entries(Ah, xgh, rows, g, g, "col")
+    del Ah
+    ref["spmv_lap3d"] = oracle.csr_spmv(lap[0], lap[1], lap[2], xl32.cpu())
+    ref["spmv_powerlaw"] = oracle.csr_spmv(pl[0], pl[1], pl[2], xp32.cpu())
+
+    def rel(got, r):
+        return float(np.linalg.norm(got - r) / np.linalg.norm(r))
+
+    out = {}
+    base = {}
+    for storage in ("f32", "bf16", "f16"):
+        dt = synth.torch_dtype(storage)
+        es = torch.tensor([], dtype=dt).element_size()
+        y, z = y32.to(dt), z32.to(dt)
+        x = torch.empty_like(y)
+        A, xg = A32.to(dt), xg32.to(dt)
+        Am = A.view(g, g)
+        rp_l, ci_l, v_l = lap[0].to(dev), lap[1].to(dev), lap[2].to(dev).to(dt)
+        rp_p, ci_p, v_p = pl[0].to(dev), pl[1].to(dev), pl[2].to(dev).to(dt)
+        xl, xp = xl32.to(dt), xp32.to(dt)
+        ws = torch.zeros(1 << 22, dtype=torch.uint8, device=dev)
+        yo = torch.empty(g, dtype=dt, device=dev)
+        sl = torch.empty(rp_l.numel() - 1, dtype=dt, device=dev)
+        sp = torch.empty(rp_p.numel() - 1, dtype=dt, device=dev)
+        cases = {
+            "axpy": (lambda: lak.vec_axpy(x, y, z, 0.5), 3 * n * es),
+            "dot": (lambda: lak.vec_dot(y, z, workspace=ws), 2 * n * es),
+            "gemv_row": (lambda: lak.dense_gemv(Am, xg, y=yo), (g * g + 2 * g) * es),
+            "gemv_col": (lambda: lak.dense_gemv(Am.t(), xg, y=yo, workspace=ws), (g * g + 2 * g) * es),
+            "spmv_lap3d": (lambda: lak.csr_spmv(rp_l, ci_l, v_l, xl, y=sl),
+                           v_l.numel() * (es + 4) + rp_l.numel() * 4 + 2 * sl.numel() * es),
+            "spmv_powerlaw": (lambda: lak.csr_spmv(rp_p, ci_p, v_p, xp, y=sp),
+                              v_p.numel() * (es + 4) + rp_p.numel() * 4 + 2 * sp.numel() * es),
+        }
+        for name, (fn, nbytes) in cases.items():
+            for _ in range(3):
+                fn()
+            ms = _median_ms(fn, reps, flush)
+            # error of this launch's result
+            if name == "axpy":
+                fn()
+                got = oracle.widen(x.cpu())[idx]
+                err = rel(got, ref["axpy"])
+            elif name == "dot":
+                d = fn().item()
+                err = abs(d - ref["dot"]) / dot_scale
+            elif name in ("gemv_row", "gemv_col"):
+                got = oracle.widen(fn().cpu())[rows]
+                err = rel(got, ref[name])
+            else:
+                err = rel(oracle.widen(fn().cpu()), ref[name])
+            rec = {"us": round(ms * 1e3, 2), "GBs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                   "err": err}
+            if storage == "f32":
+                base[name] = ms
+            else:
+                rec["time_vs_f32"] = round(ms / base[name], 4)
+            out.setdefault(name, {})[storage] = rec
+        del y, z, x, A, Am, xg, v_l, v_p, xl, xp
+    out["error_definition"] = ("norm-wise relative error vs the FP64 oracle on the original FP32 "
+                               "data (dot: |s-s*| / (||x|| ||y||)); stated bound 1e-2 for BF16")
+
+    # compensated vs plain inner product on mixed magnitudes
+    a = synth.device_mixed_magnitude_(torch.empty(n, device=dev), 908)
+    b = synth.device_mixed_magnitude_(torch.empty(n, device=dev), 909)
+    ws = torch.zeros(1 << 22, dtype=torch.uint8, device=dev)
+    ah, bh = a.cpu(), b.cpu()
+    r = oracle.dot(ah, bh)
+    abs_sum = float(np.abs(ah.double().numpy() * bh.double().numpy()).sum())
+    del ah, bh
+    comp = {}
+    for label, fn in (("plain_f32", lambda: lak.vec_dot(a, b, workspace=ws)),
+                      ("compensated_f32", lambda: lak.vec_dot_compensated(a, b, workspace=ws))):
+        for _ in range(3):
+            fn()
+        ms = _median_ms(fn, reps, flush)
+        v = fn().item()
+        comp[label] = {"us": round(ms * 1e3, 2), "GBs": round(2 * n * 4 / (ms * 1e-3) / 1e9, 1),
+                       "rel_err": abs(v - r) / abs(r), "err_over_abs_sum": abs(v - r) / abs_sum}
+    comp["time_compensated_vs_plain"] = round(comp["compensated_f32"]["us"] /
+                                              comp["plain_f32"]["us"], 4)
+    out["dot_mixed_magnitude_1e8"] = comp
+    return out
+
+
 def run_gb300(args):
     import torch
 
@@ -585,6 +726,10 @@ def run_gb300(args):
         e2e = run_e2e(items, keep, stream, device, max(1, min(K, args.e2e_steps)), lib_check,
                       dist)
 
+    precision = None
+    if not args.no_precision and not args.only and rank == 0:
+        precision = run_precision(device)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -604,6 +749,8 @@ def run_gb300(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if precision is not None:
+        line["precision"] = precision
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -668,6 +815,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the BF16/FP16-storage and compensated-dot report")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")

@@ -174,6 +174,22 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
                            const lak_cfg *cfg, void *stream);
 
 /*
+ * vec_dot_compensated: *out = sum_i x[i] * y[i] for FP32, BF16 or FP16 storage,
+ * accumulated with compensated FP32 arithmetic (the inner product of Sec. 2;
+ * the scheme is Ogita, Rump and Oishi's Dot2, 2005): each product is split
+ * exactly with one FMA and each running sum with TwoSum, the error terms are
+ * carried alongside, and the per-thread (sum, error) pairs are combined in FP64.
+ * The result behaves as if accumulated in about twice FP32 precision, so
+ * cancellation among terms of widely different magnitude costs far less
+ * accuracy than in vec_dot.  `out` is one DEVICE double.  Workspace as for
+ * vec_dot (vec_dot_workspace gives its size).  F64 storage returns LAK_EDTYPE
+ * (vec_dot already accumulates FP64 data in FP64).  n = 0 writes 0.
+ */
+LAK_API lak_status vec_dot_compensated(double *out, const void *x, const void *y, int64_t n,
+                                       lak_dtype dtype, void *workspace, size_t ws_bytes,
+                                       const lak_cfg *cfg, void *stream);
+
+/*
  * vec_dot_noalloc: the same inner product as vec_dot (same kernel, result and
  * tolerance), for callers that cannot give the library scratch memory -- for
  * instance a host application whose own memory manager owns every device

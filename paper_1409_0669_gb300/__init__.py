@@ -23,7 +23,8 @@ import torch
 from . import _native
 from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
-__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "vec_dot_noalloc", "dense_gemv",
+__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
+           "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "resolve_cfg", "set_default_cfg", "Cfg",
            "LakError", "storage_of", "library_path"]
 
@@ -179,6 +180,31 @@ def vec_dot(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None
                       _dev_ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                       _cfg_ptr(cfg), sh)
     _native.check("vec_dot", st)
+    return out
+
+
+def vec_dot_compensated(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None,
+                        workspace: Optional[torch.Tensor] = None, cfg: CfgLike = None,
+                        stream=None) -> torch.Tensor:
+    """<x, y> for FP32/BF16/FP16 storage with compensated (Dot2) FP32
+    accumulation and an FP64 combine; the result is a one-element float64
+    device tensor."""
+    s = _same_storage(x, y)
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y must have the same length")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    elif out.dtype != torch.float64 or out.numel() < 1:
+        raise TypeError("out must be a float64 tensor with at least one element")
+    sh = _stream(stream)
+    need = vec_dot_workspace(n, s, cfg)
+    if workspace is None:
+        workspace = _workspace(need, sh, x.device)
+    st = _lib.vec_dot_compensated(_dev_ptr(out, "out"), _vec_arg(x, "x"), _vec_arg(y, "y"), n,
+                                  DTYPES[s], _dev_ptr(workspace, "workspace"),
+                                  workspace.numel() * workspace.element_size(), _cfg_ptr(cfg), sh)
+    _native.check("vec_dot_compensated", st)
     return out
 
 

@@ -23,7 +23,8 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 
 # exported symbols, in header order (checked by the ABI test)
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
-           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_noalloc",
+           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
+           "vec_dot_noalloc",
            "dense_gemv_workspace", "dense_gemv", "csr_spmv")
 
 
@@ -61,6 +62,7 @@ _SIGNATURES = {
     "vec_dot_workspace": (_SZ, [_I64, _I32, _CFGP]),
     "vec_dot": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "vec_dot_noalloc": (_I32, [_P, _P, _P, _I64, _I32, _CFGP, _P]),
+    "vec_dot_compensated": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
     "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
     "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),

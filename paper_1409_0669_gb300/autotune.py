@@ -9,7 +9,8 @@ GB300 the same four axes become:
   grid       automatic (enough blocks to cover the data once) or a multiple of
              the SM count (1, 2, 4, 8, 16, 32 blocks per SM: persistent grids)
 Each configuration is timed with CUDA events on the launching stream (median
-of `reps` launches, L2 flushed between launches when the operands fit in it).
+of `reps` launches; when the operands fit in L2, a 256 MB buffer is read before
+each launch to evict them).
 
 `copy_first_study` repeats the paper's central experiment (Sec. 3.2, 3.4):
 tune the copy kernel exhaustively, keep the configurations within 15 % of the
@@ -142,7 +143,7 @@ class Problem:
         ev1 = torch.cuda.Event(enable_timing=True)
         for _ in range(reps):
             if self.flush is not None:
-                self.flush.zero_()
+                self.flush.sum()          # evicts L2 without leaving dirty lines
             ev0.record(self.stream)
             st = self.fn(cptr)
             ev1.record(self.stream)

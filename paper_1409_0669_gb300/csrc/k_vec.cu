@@ -174,6 +174,89 @@ dot_kernel(void *out, const T *__restrict__ x, const T *__restrict__ y, int64_t 
     }
 }
 
+// ---- compensated dot (FP32 arithmetic on FP32 / BF16 / FP16 storage) --------
+//
+// Per thread, V running sums carried as (s, c): every product is split exactly
+// into p + e with one FMA (TwoProduct) and every addition into s' + f with
+// Knuth's TwoSum, the errors e and f collecting in c (Ogita, Rump and Oishi's
+// Dot2 in FP32: the sum behaves as if accumulated in twice FP32 precision).
+// Each (s, c) pair is then added as an exact double, and the warp, block and
+// last-block combines run in FP64 as in dot_kernel.  The result is written as
+// a double.
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+dot_comp_kernel(double *out, const T *__restrict__ x, const T *__restrict__ y, int64_t n,
+                int64_t head, int64_t nchunks, int inc, unsigned int *counter,
+                double *partials) {
+    __shared__ double wsum[32];
+    __shared__ int am_last;
+    float sv[V], cv[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) sv[v] = cv[v] = 0.0f;
+
+    auto add = [](float &s, float &c, float a, float b) {
+        const float p = a * b;
+        const float e = __fmaf_rn(a, b, -p);      // a*b = p + e exactly
+        const float t = s + p;                    // TwoSum(s, p) = t + f
+        const float bv = t - s;
+        const float f = (s - (t - bv)) + (p - bv);
+        s = t;
+        c += f + e;
+    };
+
+    const Range r = chunk_range(nchunks, inc);
+    for (int64_t ch = r.begin; ch < r.end; ch += r.stride) {
+        const int64_t o = head + ch * V;
+        Pack<T, V> px, py;
+        load_pack<T, V, STREAM>(px, x + o);
+        load_pack<T, V, STREAM>(py, y + o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) add(sv[v], cv[v], widen(px.e[v]), widen(py.e[v]));
+    }
+    {
+        const int64_t body_end = head + nchunks * V;
+        const int64_t nextra = head + (n - body_end);
+        const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < nextra) {
+            const int64_t i = extra_index(t, head, body_end);
+            add(sv[0], cv[0], widen(x[i]), widen(y[i]));
+        }
+    }
+    double d = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) d += (double)sv[v] + (double)cv[v];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    d = group_sum(d, 32);
+    if (lane == 0) wsum[warp] = d;
+    __syncthreads();
+    if (warp == 0) {
+        double b = lane < nwarps ? wsum[lane] : 0.0;
+        b = group_sum(b, 32);
+        if (lane == 0) {
+            partials[blockIdx.x] = b;
+            __threadfence();
+            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
+            am_last = (ticket == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
+    v = group_sum(v, 32);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double f = lane < nwarps ? wsum[lane] : 0.0;
+        f = group_sum(f, 32);
+        if (lane == 0) *out = f;
+    }
+}
+
 // ---- dispatch ----------------------------------------------------------------
 
 template <typename E>
@@ -234,6 +317,30 @@ lak_status dot_t(int vec, void *out, const void *x, const void *y, int64_t n, in
     return check_launch("vec_dot");
 }
 
+template <typename T>
+lak_status dot_comp_t(int vec, void *out, const void *x, const void *y, int64_t n, int64_t head,
+                      void *ws, const Launch &L, cudaStream_t s) {
+    const T *xp = static_cast<const T *>(x);
+    const T *yp = static_cast<const T *>(y);
+    double *o = static_cast<double *>(out);
+    unsigned int *counter = static_cast<unsigned int *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
+    const int64_t nchunks = (n - head) / vec;
+#define LAK_DOTC(VV)                                                                    \
+    dot_comp_kernel<T, VV><<<L.grid, L.block, 0, s>>>(o, xp, yp, n, head, nchunks, L.inc, \
+                                                      counter, partials)
+    switch (vec) {
+    case 1: LAK_DOTC(1); break;
+    case 2: LAK_DOTC(2); break;
+    case 4: LAK_DOTC(4); break;
+    case 8: LAK_DOTC(8); break;
+    case 16: LAK_DOTC(16); break;
+    default: return fail(LAK_EINVAL, "vec_dot_compensated: unsupported vec %d", vec);
+    }
+#undef LAK_DOTC
+    return check_launch("vec_dot_compensated");
+}
+
 }  // namespace
 
 lak_status launch_copy(void *x, const void *y, int64_t n, int es, const Launch &L, int64_t head,
@@ -266,6 +373,22 @@ lak_status launch_dot(lak_dtype dt, void *out, const void *x, const void *y, int
     case LAK_F16: return dot_t<__half>(L.vec, out, x, y, n, head, ws, L, s);
     }
     return fail(LAK_EDTYPE, "vec_dot: unknown dtype %d", (int)dt);
+}
+
+}  // namespace lak
+
+namespace lak {
+
+lak_status launch_dot_comp(lak_dtype dt, void *out, const void *x, const void *y, int64_t n,
+                           void *ws, const Launch &L, int64_t head, cudaStream_t s) {
+    switch (dt) {
+    case LAK_F32: return dot_comp_t<float>(L.vec, out, x, y, n, head, ws, L, s);
+    case LAK_BF16: return dot_comp_t<__nv_bfloat16>(L.vec, out, x, y, n, head, ws, L, s);
+    case LAK_F16: return dot_comp_t<__half>(L.vec, out, x, y, n, head, ws, L, s);
+    default: break;
+    }
+    return fail(LAK_EDTYPE, "vec_dot_compensated: FP32, BF16 or FP16 storage only (dtype %d)",
+                (int)dt);
 }
 
 }  // namespace lak

@@ -506,6 +506,39 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n, l
     return launch_dot(dtype, out, x, y, n, workspace, p.L, p.head, s);
 }
 
+LAK_API lak_status vec_dot_compensated(double *out, const void *x, const void *y, int64_t n,
+                                       lak_dtype dtype, void *workspace, size_t ws_bytes,
+                                       const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_dot_compensated", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (dtype == LAK_F64)
+        return fail(LAK_EDTYPE, "vec_dot_compensated: FP32, BF16 or FP16 storage only");
+    if (n < 0) return fail(LAK_EINVAL, "vec_dot_compensated: n=%lld < 0", (long long)n);
+    if (!out || (uintptr_t)out % 8) return fail(LAK_EINVAL, "vec_dot_compensated: bad out");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        const cudaError_t e = cudaMemsetAsync(out, 0, 8, s);
+        if (e != cudaSuccess)
+            return fail(LAK_ECUDA, "vec_dot_compensated: memset: %s", cudaGetErrorString(e));
+        return LAK_OK;
+    }
+    const int es = esize(dtype);
+    if (!x || !y) return fail(LAK_EINVAL, "vec_dot_compensated: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es))
+        return fail(LAK_EINVAL, "vec_dot_compensated: pointers not aligned to the element size");
+    const void *ptrs[2] = {x, y};
+    VecPlan p;
+    st = plan_vector(LAK_OP_DOT, dtype, n, cfg, ptrs, 2, &p);
+    if (st != LAK_OK) return st;
+    const size_t need = (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)p.L.grid;
+    if (!workspace || ws_bytes < need)
+        return fail(LAK_EWORKSPACE, "vec_dot_compensated: workspace of %zu bytes needed, %zu given",
+                    need, workspace ? ws_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256)
+        return fail(LAK_EWORKSPACE, "vec_dot_compensated: workspace not 256-byte aligned");
+    return launch_dot_comp(dtype, out, x, y, n, workspace, p.L, p.head, s);
+}
+
 LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout, lak_dtype dtype,
                                     const lak_cfg *cfg) {
     if (!valid_dtype(dtype) || m < 0 || n < 0 || check_cfg(cfg, "dense_gemv_workspace") != LAK_OK)

@@ -74,6 +74,8 @@ lak_status launch_axpy(lak_dtype dt, void *x, const void *y, const void *z, doub
                        int64_t n, const Launch &L, int64_t head, cudaStream_t s);
 lak_status launch_dot(lak_dtype dt, void *out, const void *x, const void *y, int64_t n,
                       void *ws, const Launch &L, int64_t head, cudaStream_t s);
+lak_status launch_dot_comp(lak_dtype dt, void *out, const void *x, const void *y, int64_t n,
+                           void *ws, const Launch &L, int64_t head, cudaStream_t s);
 lak_status launch_gemv_row(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
                            int64_t n, int64_t lda, const Launch &L, int group, cudaStream_t s);
 lak_status launch_gemv_col(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,

@@ -249,3 +249,15 @@ def device_normal_(out: torch.Tensor, seed: int):
         tmp.normal_(0.0, 1.0, generator=g)
         out.copy_(tmp)
     return out
+
+
+def device_mixed_magnitude_(out: torch.Tensor, seed: int, lo_exp: float = -4.0,
+                            hi_exp: float = 4.0):
+    """Fill `out` in place with random signs and magnitudes log-uniform in
+    [10^lo_exp, 10^hi_exp] (Philox, seeded)."""
+    g = torch.Generator(device=out.device).manual_seed(seed)
+    e = torch.empty(out.shape, dtype=torch.float64, device=out.device).uniform_(lo_exp, hi_exp,
+                                                                                  generator=g)
+    sign = torch.randint(0, 2, out.shape, generator=g, device=out.device).to(torch.float64) * 2 - 1
+    out.copy_(sign * torch.pow(10.0, e))
+    return out
