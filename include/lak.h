@@ -270,6 +270,58 @@ LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_
                             int64_t nnz, lak_dtype dtype, const lak_cfg *cfg,
                             void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched operations: many independent instances of uneven sizes in one
+ * persistent launch (an extension of this library; the paper runs one
+ * operation at a time).
+ *
+ * Two steps, so that the launch itself reads nothing from the host and can be
+ * replayed (for instance from a CUDA graph) as often as wanted:
+ *   1. lak_batch_plan (host only, no CUDA call): from the caller's instance
+ *      descriptors (in HOST memory) it writes a work table into a caller host
+ *      buffer -- a header, per-instance prefix offsets of work units and the
+ *      descriptors with their per-instance launch details -- and fills a
+ *      lak_batch_info.  Called with table = NULL it only fills the info
+ *      (table and workspace sizes).  Work units hold about the same number of
+ *      bytes, so uneven instances are balanced across the persistent grid.
+ *   2. The caller copies the table to device memory (any 8-byte aligned
+ *      buffer) and calls lak_batch_run with it and a workspace of
+ *      info->workspace_bytes (laid out like every workspace: zero-filled counter
+ *      area first).  Pointers inside the descriptors must stay valid and the
+ *      operands must not overlap across instances.
+ * Ops: LAK_OP_AXPY (lak_axpy_desc), LAK_OP_DOT (lak_dot_desc; `out` is float
+ * for F32/BF16/F16, double for F64), LAK_OP_GEMV_ROW (lak_gemv_desc, row-major
+ * instances), LAK_OP_SPMV (lak_csr_desc, warp-segmented rows).  Per instance
+ * the results equal those of the single-instance calls up to the order of
+ * floating-point summation (axpy: identical).  The dot keeps at most
+ * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).
+ * ---------------------------------------------------------------------- */
+typedef struct { void *x; const void *y; const void *z; int64_t n; double alpha; } lak_axpy_desc;
+typedef struct { void *out; const void *x; const void *y; int64_t n; } lak_dot_desc;
+typedef struct { void *y; const void *A; const void *x; int64_t m; int64_t n; int64_t lda; } lak_gemv_desc;
+typedef struct {
+    void *y; const int32_t *row_ptr; const int32_t *col_idx; const void *vals; const void *x;
+    int64_t m; int64_t n; int64_t nnz;
+} lak_csr_desc;
+
+typedef struct {
+    int64_t count;          /* instances */
+    int64_t total_units;    /* work units over all instances */
+    int64_t unit_elems;     /* elements (or rows, for GEMV / SpMV) per unit */
+    size_t table_bytes;     /* size of the work table */
+    size_t workspace_bytes; /* device workspace lak_batch_run needs */
+    lak_cfg cfg;            /* resolved launch configuration */
+    int32_t op;
+    int32_t dtype;
+} lak_batch_info;
+
+LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_descs, int64_t count,
+                                  const lak_cfg *cfg, void *host_table, size_t table_bytes,
+                                  lak_batch_info *info);
+
+LAK_API lak_status lak_batch_run(const lak_batch_info *info, const void *dev_table, void *workspace,
+                                 size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
            "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
            "vec_dot_noalloc",
-           "dense_gemv_workspace", "dense_gemv", "csr_spmv")
+           "dense_gemv_workspace", "dense_gemv", "csr_spmv", "lak_batch_plan", "lak_batch_run")
 
 
 class LakCfg(ctypes.Structure):
@@ -38,6 +38,34 @@ class LakCfg(ctypes.Structure):
 
     def __repr__(self):
         return "LakCfg(block=%d, grid=%d, vec=%d, increment=%d)" % self.as_tuple()
+
+
+class AxpyDesc(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("alpha", ctypes.c_double)]
+
+
+class DotDesc(ctypes.Structure):
+    _fields_ = [("out", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+class GemvDesc(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("A", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64)]
+
+
+class CsrDesc(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("total_units", ctypes.c_int64),
+                ("unit_elems", ctypes.c_int64), ("table_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t), ("cfg", LakCfg),
+                ("op", ctypes.c_int32), ("dtype", ctypes.c_int32)]
 
 
 class LakError(RuntimeError):
@@ -66,6 +94,8 @@ _SIGNATURES = {
     "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
     "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
     "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
+    "lak_batch_plan": (_I32, [_I32, _I32, _P, _I64, _CFGP, _P, _SZ, ctypes.POINTER(BatchInfo)]),
+    "lak_batch_run": (_I32, [ctypes.POINTER(BatchInfo), _P, _P, _SZ, _P]),
 }
 
 _lib = None

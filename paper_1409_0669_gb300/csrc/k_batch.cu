@@ -1,0 +1,493 @@
+// Batched operations: many independent instances of uneven sizes in one
+// persistent launch.
+//
+// lak_batch_plan (host, no CUDA call) splits every instance into work units of
+// about the same size -- `unit_elems` elements of a vector, a run of rows of a
+// dense matrix with about as many entries, or one block's worth of 32-row CSR
+// blocks -- and writes a table: a header, the exclusive prefix of units per
+// instance, and per-instance items (the caller's descriptor plus the launch
+// details the plan chose).  lak_batch_run launches one persistent grid over
+// all units; a block maps its unit to an instance with a binary search over
+// the prefix (a few L1-resident loads) and runs the same inner loops as the
+// single-instance kernels.  Batched dot products finish per instance with the
+// last-arriving-unit combine (an arrival counter per instance in the workspace
+// counter area), in unit order, so results are deterministic.
+#include <cstddef>
+
+#include "lak_internal.cuh"
+#include "spmv_seg.cuh"
+
+namespace lak {
+namespace {
+
+struct BatchHead {
+    int64_t count;
+    int64_t total_units;
+    int64_t unit_elems;
+    int32_t op;
+    int32_t dtype;
+    int32_t vec;
+    int32_t block;
+};
+
+struct AxpyItem {
+    lak_axpy_desc d;
+    int64_t units;
+    int32_t vec_ok;
+    int32_t pad;
+};
+struct DotItem {
+    lak_dot_desc d;
+    int64_t units;
+    int32_t vec_ok;
+    int32_t pad;
+};
+struct GemvItem {
+    lak_gemv_desc d;
+    int64_t rows_per_unit;
+    int32_t vec_ok;
+    int32_t pad;
+};
+struct CsrItem {
+    lak_csr_desc d;
+    int64_t units;
+    int32_t vec_ok;
+    int32_t pad;
+};
+
+constexpr size_t kHeadBytes = 64;
+static_assert(sizeof(BatchHead) <= kHeadBytes, "batch header");
+
+size_t offsets_bytes(int64_t count) { return (size_t)(count + 1) * 8; }
+size_t items_offset(int64_t count) { return (kHeadBytes + offsets_bytes(count) + 15) / 16 * 16; }
+
+size_t item_size(lak_op op) {
+    switch (op) {
+    case LAK_OP_AXPY: return sizeof(AxpyItem);
+    case LAK_OP_DOT: return sizeof(DotItem);
+    case LAK_OP_GEMV_ROW: return sizeof(GemvItem);
+    case LAK_OP_SPMV: return sizeof(CsrItem);
+    default: return 0;
+    }
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+bool aligned_to(const void *p, int w) { return (uintptr_t)p % (uintptr_t)w == 0; }
+
+// ---- device helpers ----------------------------------------------------------
+
+// largest i in [0, count) with offs[i] <= u (skips instances without units)
+__device__ __forceinline__ int64_t find_instance(const int64_t *offs, int64_t count, int64_t u) {
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+axpy_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
+                  const AxpyItem *__restrict__ items) {
+    using A = typename Acc<T>::type;
+    const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int64_t i = find_instance(offs, count, u);
+        const AxpyItem it = items[i];
+        T *x = static_cast<T *>(it.d.x);
+        const T *y = static_cast<const T *>(it.d.y);
+        const T *z = static_cast<const T *>(it.d.z);
+        const A alpha = static_cast<A>(it.d.alpha);
+        const int64_t b = (u - __ldg(offs + i)) * ue;
+        const int64_t e = b + ue < it.d.n ? b + ue : it.d.n;
+        int64_t k = b;
+        if (it.vec_ok) {
+            const int64_t nfull = (e - b) / V;
+            for (int64_t c = threadIdx.x; c < nfull; c += blockDim.x) {
+                const int64_t o = b + c * V;
+                Pack<T, V> py, pz, px;
+                load_pack<T, V, COHERENT>(py, y + o);
+                load_pack<T, V, COHERENT>(pz, z + o);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    px.e[v] = narrow<T>(fma_acc(alpha, widen(pz.e[v]), widen(py.e[v])));
+                store_pack<T, V>(x + o, px);
+            }
+            k = b + nfull * V;
+        }
+        for (int64_t j = k + threadIdx.x; j < e; j += blockDim.x)
+            x[j] = narrow<T>(fma_acc(alpha, widen(z[j]), widen(y[j])));
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
+                 const DotItem *__restrict__ items, unsigned int *tickets, double *partials) {
+    using A = typename Acc<T>::type;
+    __shared__ double wsum[32];
+    const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int64_t i = find_instance(offs, count, u);
+        const DotItem it = items[i];
+        const T *x = static_cast<const T *>(it.d.x);
+        const T *y = static_cast<const T *>(it.d.y);
+        const int64_t u0 = __ldg(offs + i);
+        const int64_t b = (u - u0) * ue;
+        const int64_t e = b + ue < it.d.n ? b + ue : it.d.n;
+        A acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = A(0);
+        int64_t k = b;
+        if (it.vec_ok) {
+            const int64_t nfull = (e - b) / V;
+            for (int64_t c = threadIdx.x; c < nfull; c += blockDim.x) {
+                const int64_t o = b + c * V;
+                Pack<T, V> px, py;
+                load_pack<T, V, STREAM>(px, x + o);
+                load_pack<T, V, STREAM>(py, y + o);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    acc[v] = fma_acc(widen(px.e[v]), widen(py.e[v]), acc[v]);
+            }
+            k = b + nfull * V;
+        }
+        for (int64_t j = k + threadIdx.x; j < e; j += blockDim.x)
+            acc[0] = fma_acc(widen(x[j]), widen(y[j]), acc[0]);
+#pragma unroll
+        for (int w = 1; w < V; w <<= 1) {
+#pragma unroll
+            for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+        }
+        const A s = group_sum(acc[0], 32);
+        if (lane == 0) wsum[warp] = (double)s;
+        __syncthreads();
+        if (warp == 0) {
+            double bsum = lane < nwarps ? wsum[lane] : 0.0;
+            bsum = group_sum(bsum, 32);
+            if (lane == 0) {
+                partials[u] = bsum;
+                __threadfence();
+                const unsigned int last = (unsigned int)(it.units - 1);
+                if (atomicInc(tickets + i, last) == last) {
+                    __threadfence();
+                    double f = 0.0;                       // unit order: deterministic
+                    for (int64_t q = 0; q < it.units; ++q) f += __ldcg(partials + u0 + q);
+                    if constexpr (sizeof(A) == 8)
+                        *static_cast<double *>(it.d.out) = f;
+                    else
+                        *static_cast<float *>(it.d.out) = __double2float_rn(f);
+                }
+            }
+        }
+        __syncthreads();                                  // wsum is reused
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
+                  const GemvItem *__restrict__ items) {
+    using A = typename Acc<T>::type;
+    const int64_t count = head->count, total = head->total_units;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int64_t i = find_instance(offs, count, u);
+        const GemvItem it = items[i];
+        const T *Am = static_cast<const T *>(it.d.A);
+        const T *x = static_cast<const T *>(it.d.x);
+        T *y = static_cast<T *>(it.d.y);
+        const int64_t n = it.d.n, lda = it.d.lda;
+        const int64_t r0 = (u - __ldg(offs + i)) * it.rows_per_unit;
+        const int64_t r1 = r0 + it.rows_per_unit < it.d.m ? r0 + it.rows_per_unit : it.d.m;
+        for (int64_t row = r0 + warp; row < r1; row += nwarps) {   // warp-uniform
+            const T *Ar = Am + row * lda;
+            A acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = A(0);
+            int64_t k = 0;
+            if (it.vec_ok) {
+                const int64_t nch = n / V;
+#pragma unroll 4
+                for (int64_t c = lane; c < nch; c += 32) {
+                    Pack<T, V> pa, px;
+                    load_pack<T, V, STREAM>(pa, Ar + c * V);
+                    load_pack<T, V, CACHED>(px, x + c * V);
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        acc[v] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[v]);
+                }
+                k = nch * V;
+            }
+            for (int64_t j = k + lane; j < n; j += 32)
+                acc[0] = fma_acc(widen(Ar[j]), widen(ld_cached(x + j)), acc[0]);
+#pragma unroll
+            for (int w = 1; w < V; w <<= 1) {
+#pragma unroll
+                for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+            }
+            const A s = group_sum(acc[0], 32);
+            if (lane == 0) y[row] = narrow<T>(s);
+        }
+    }
+}
+
+template <typename T, int U>
+__global__ void __launch_bounds__(512)
+spmv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
+                  const CsrItem *__restrict__ items) {
+    using Ac = typename Acc<T>::type;
+    __shared__ int64_t rs_all[16][33];
+    __shared__ Ac racc_all[16][32];
+    const int64_t count = head->count, total = head->total_units;
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int64_t i = find_instance(offs, count, u);
+        const CsrItem it = items[i];
+        const int64_t b = (u - __ldg(offs + i)) * wpb + warp;    // this warp's 32-row block
+        if (b * 32 >= it.d.m) continue;                             // warp-uniform
+        const int64_t nnz = __ldg(it.d.row_ptr + it.d.m);
+        if (it.vec_ok)
+            seg_rows32<T, U, true>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
+                                   static_cast<const T *>(it.d.vals),
+                                   static_cast<const T *>(it.d.x), it.d.m, nnz, b, rs_all[warp],
+                                   racc_all[warp]);
+        else
+            seg_rows32<T, U, false>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
+                                    static_cast<const T *>(it.d.vals),
+                                    static_cast<const T *>(it.d.x), it.d.m, nnz, b, rs_all[warp],
+                                    racc_all[warp]);
+    }
+}
+
+// ---- host side ---------------------------------------------------------------
+
+template <typename T>
+lak_status run_typed(const lak_batch_info &info, const char *table, void *ws, dim3 grid,
+                     int block, cudaStream_t s) {
+    const BatchHead *head = reinterpret_cast<const BatchHead *>(table);
+    const int64_t *offs = reinterpret_cast<const int64_t *>(table + kHeadBytes);
+    const char *items = table + items_offset(info.count);
+    const int vec = info.cfg.vec;
+#define LAK_VECSW(KERNEL, ...)                                                              \
+    switch (vec) {                                                                          \
+    case 1: KERNEL<T, 1><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
+    case 2: KERNEL<T, 2><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
+    case 4: KERNEL<T, 4><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
+    case 8: KERNEL<T, 8><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
+    case 16: KERNEL<T, 16><<<grid, block, 0, s>>>(__VA_ARGS__); break;                      \
+    default: return fail(LAK_EINVAL, "lak_batch_run: unsupported vec %d", vec);             \
+    }
+    switch ((lak_op)info.op) {
+    case LAK_OP_AXPY:
+        LAK_VECSW(axpy_batch_kernel, head, offs, reinterpret_cast<const AxpyItem *>(items));
+        break;
+    case LAK_OP_DOT: {
+        unsigned int *tickets = static_cast<unsigned int *>(ws);
+        double *partials =
+            reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
+        LAK_VECSW(dot_batch_kernel, head, offs, reinterpret_cast<const DotItem *>(items), tickets,
+                  partials);
+        break;
+    }
+    case LAK_OP_GEMV_ROW:
+        LAK_VECSW(gemv_batch_kernel, head, offs, reinterpret_cast<const GemvItem *>(items));
+        break;
+    case LAK_OP_SPMV:
+        LAK_VECSW(spmv_batch_kernel, head, offs, reinterpret_cast<const CsrItem *>(items));
+        break;
+    default: return fail(LAK_EINVAL, "lak_batch_run: unsupported op %d", info.op);
+    }
+#undef LAK_VECSW
+    return check_launch("lak_batch_run");
+}
+
+}  // namespace
+}  // namespace lak
+
+using namespace lak;
+
+extern "C" {
+
+LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_descs, int64_t count,
+                                  const lak_cfg *cfg, void *host_table, size_t table_bytes,
+                                  lak_batch_info *info) {
+    if (!info) return fail(LAK_EINVAL, "lak_batch_plan: NULL info");
+    if (op != LAK_OP_AXPY && op != LAK_OP_DOT && op != LAK_OP_GEMV_ROW && op != LAK_OP_SPMV)
+        return fail(LAK_EINVAL, "lak_batch_plan: op %d has no batched form", (int)op);
+    if (dtype != LAK_F32 && dtype != LAK_F64 && dtype != LAK_BF16 && dtype != LAK_F16)
+        return fail(LAK_EDTYPE, "lak_batch_plan: unknown dtype %d", (int)dtype);
+    if (count < 0 || (count > 0 && !host_descs))
+        return fail(LAK_EINVAL, "lak_batch_plan: bad count or NULL descriptors");
+    if (op == LAK_OP_DOT && count > LAK_WS_COUNTER_BYTES / 4)
+        return fail(LAK_EINVAL, "lak_batch_plan: at most %d dot instances per batch",
+                    LAK_WS_COUNTER_BYTES / 4);
+    if (cfg && cfg->block != 0 &&
+        (cfg->block < 32 || cfg->block > 512 || cfg->block % 32 || cfg->grid < 0 ||
+         (cfg->vec != 0 && cfg->vec != 1 && cfg->vec != 2 && cfg->vec != 4 && cfg->vec != 8 &&
+          cfg->vec != 16)))
+        return fail(LAK_EINVAL, "lak_batch_plan: invalid cfg");
+    const lak_cfg c = base_config(op, dtype, cfg);
+    int vec = c.vec;
+    if (op == LAK_OP_SPMV) vec = vec < 4 ? 4 : (vec > 8 ? 8 : vec);   // seg rows: 4..8 entries
+    const int es = esize(dtype);
+    const int w = access_bytes(vec, es);
+    const int64_t ue = (int64_t)c.block * vec * 4;                  // ~4 passes per thread
+    const size_t isz = item_size(op);
+    const size_t need = items_offset(count) + isz * (size_t)count;
+
+    // units per instance
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        int64_t units = 0;
+        switch (op) {
+        case LAK_OP_AXPY: {
+            const lak_axpy_desc &d = static_cast<const lak_axpy_desc *>(host_descs)[i];
+            if (d.n < 0) return fail(LAK_EINVAL, "lak_batch_plan: instance %lld: n < 0", (long long)i);
+            units = cdiv(d.n, ue);
+            break;
+        }
+        case LAK_OP_DOT: {
+            const lak_dot_desc &d = static_cast<const lak_dot_desc *>(host_descs)[i];
+            if (d.n < 0) return fail(LAK_EINVAL, "lak_batch_plan: instance %lld: n < 0", (long long)i);
+            units = d.n > 0 ? cdiv(d.n, ue) : 1;        // an empty dot still writes 0
+            break;
+        }
+        case LAK_OP_GEMV_ROW: {
+            const lak_gemv_desc &d = static_cast<const lak_gemv_desc *>(host_descs)[i];
+            if (d.m < 0 || d.n < 0 || d.lda < (d.n > 1 ? d.n : 1))
+                return fail(LAK_EINVAL, "lak_batch_plan: instance %lld: bad m, n or lda", (long long)i);
+            const int64_t rpu = d.n > 0 ? (cdiv(ue, d.n) < d.m ? cdiv(ue, d.n) : d.m) : d.m;
+            units = d.m > 0 ? cdiv(d.m, rpu > 0 ? rpu : 1) : 0;
+            break;
+        }
+        case LAK_OP_SPMV: {
+            const lak_csr_desc &d = static_cast<const lak_csr_desc *>(host_descs)[i];
+            if (d.m < 0 || d.n < 0 || d.nnz < 0 || d.nnz > 0x7fffffffLL)
+                return fail(LAK_EINVAL, "lak_batch_plan: instance %lld: bad sizes", (long long)i);
+            units = cdiv(d.m, c.block);                 // (block/32) 32-row blocks per unit
+            break;
+        }
+        default: break;
+        }
+        total += units;
+    }
+    info->count = count;
+    info->total_units = total;
+    info->unit_elems = ue;
+    info->table_bytes = need;
+    info->workspace_bytes =
+        op == LAK_OP_DOT ? (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)total : 0;
+    info->cfg = lak_cfg{c.block, c.grid, vec, c.increment};
+    info->op = (int32_t)op;
+    info->dtype = (int32_t)dtype;
+    if (!host_table) return LAK_OK;
+    if (table_bytes < need)
+        return fail(LAK_EINVAL, "lak_batch_plan: table of %zu bytes needed, %zu given", need,
+                    table_bytes);
+    char *t = static_cast<char *>(host_table);
+    memset(t, 0, need);
+    BatchHead *h = reinterpret_cast<BatchHead *>(t);
+    h->count = count;
+    h->total_units = total;
+    h->unit_elems = ue;
+    h->op = (int32_t)op;
+    h->dtype = (int32_t)dtype;
+    h->vec = vec;
+    h->block = c.block;
+    int64_t *offs = reinterpret_cast<int64_t *>(t + kHeadBytes);
+    char *items = t + items_offset(count);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        offs[i] = acc;
+        switch (op) {
+        case LAK_OP_AXPY: {
+            const lak_axpy_desc &d = static_cast<const lak_axpy_desc *>(host_descs)[i];
+            AxpyItem it{};
+            it.d = d;
+            it.units = cdiv(d.n, ue);
+            it.vec_ok = aligned_to(d.x, w) && aligned_to(d.y, w) && aligned_to(d.z, w);
+            memcpy(items + isz * i, &it, sizeof it);
+            acc += it.units;
+            break;
+        }
+        case LAK_OP_DOT: {
+            const lak_dot_desc &d = static_cast<const lak_dot_desc *>(host_descs)[i];
+            DotItem it{};
+            it.d = d;
+            it.units = d.n > 0 ? cdiv(d.n, ue) : 1;
+            it.vec_ok = aligned_to(d.x, w) && aligned_to(d.y, w);
+            memcpy(items + isz * i, &it, sizeof it);
+            acc += it.units;
+            break;
+        }
+        case LAK_OP_GEMV_ROW: {
+            const lak_gemv_desc &d = static_cast<const lak_gemv_desc *>(host_descs)[i];
+            GemvItem it{};
+            it.d = d;
+            const int64_t rpu = d.n > 0 ? (cdiv(ue, d.n) < d.m ? cdiv(ue, d.n) : d.m) : d.m;
+            it.rows_per_unit = rpu > 0 ? rpu : 1;
+            it.vec_ok = aligned_to(d.A, w) && aligned_to(d.x, w) && (d.lda * es) % w == 0;
+            memcpy(items + isz * i, &it, sizeof it);
+            acc += d.m > 0 ? cdiv(d.m, it.rows_per_unit) : 0;
+            break;
+        }
+        case LAK_OP_SPMV: {
+            const lak_csr_desc &d = static_cast<const lak_csr_desc *>(host_descs)[i];
+            CsrItem it{};
+            it.d = d;
+            it.units = cdiv(d.m, c.block);
+            it.vec_ok = aligned_to(d.col_idx, 16) && aligned_to(d.vals, 16);
+            memcpy(items + isz * i, &it, sizeof it);
+            acc += it.units;
+            break;
+        }
+        default: break;
+        }
+    }
+    offs[count] = acc;
+    return LAK_OK;
+}
+
+LAK_API lak_status lak_batch_run(const lak_batch_info *info, const void *dev_table, void *workspace,
+                                 size_t ws_bytes, void *stream) {
+    if (!info) return fail(LAK_EINVAL, "lak_batch_run: NULL info");
+    if (info->count < 0 || info->total_units < 0)
+        return fail(LAK_EINVAL, "lak_batch_run: bad info");
+    if (info->total_units == 0) return LAK_OK;
+    if (!dev_table || (uintptr_t)dev_table % 16)
+        return fail(LAK_EINVAL, "lak_batch_run: table must be a 16-byte aligned device buffer");
+    if (info->workspace_bytes > 0) {
+        if (!workspace || ws_bytes < info->workspace_bytes)
+            return fail(LAK_EWORKSPACE, "lak_batch_run: workspace of %zu bytes needed, %zu given",
+                        info->workspace_bytes, workspace ? ws_bytes : (size_t)0);
+        if ((uintptr_t)workspace % 256)
+            return fail(LAK_EWORKSPACE, "lak_batch_run: workspace not 256-byte aligned");
+    }
+    const int block = info->cfg.block;
+    if (block < 32 || block > 512 || block % 32)
+        return fail(LAK_EINVAL, "lak_batch_run: bad block %d", block);
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    int64_t grid = info->cfg.grid;
+    if (grid <= 0) grid = (int64_t)di->sms * (di->max_threads_per_sm / block);
+    if (grid > info->total_units) grid = info->total_units;
+    const char *table = static_cast<const char *>(dev_table);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch ((lak_dtype)info->dtype) {
+    case LAK_F32: return run_typed<float>(*info, table, workspace, dim3((unsigned)grid), block, s);
+    case LAK_F64: return run_typed<double>(*info, table, workspace, dim3((unsigned)grid), block, s);
+    case LAK_BF16:
+        return run_typed<__nv_bfloat16>(*info, table, workspace, dim3((unsigned)grid), block, s);
+    case LAK_F16: return run_typed<__half>(*info, table, workspace, dim3((unsigned)grid), block, s);
+    }
+    return fail(LAK_EDTYPE, "lak_batch_run: unknown dtype %d", info->dtype);
+}
+
+}  // extern "C"

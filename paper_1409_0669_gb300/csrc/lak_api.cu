@@ -325,6 +325,12 @@ lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, S
 
 }  // namespace
 
+lak_cfg base_config(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
+    lak_cfg c = base_cfg(op, dt, cfg);
+    if (c.vec == 0) c.vec = builtin_default(op, dt).vec;
+    return c;
+}
+
 int pick_vec(int want, int es, const void *const *ptrs, int nptrs, int64_t n, int64_t *head) {
     for (int vec = want; vec > 1; vec >>= 1) {
         const int w = access_bytes(vec, es);

@@ -95,3 +95,13 @@ def assert_reduced_sum(got: np.ndarray, ref: np.ndarray, abs_terms: np.ndarray,
     if nref > 0:
         err = np.linalg.norm(got - ref) / nref
         assert err <= 2 * UNIT_ROUNDOFF[storage], f"{what}: norm-wise {err:.3e}"
+
+
+def assert_normwise_scaled(got, ref, abs_ref, storage: str, what=""):
+    """||got - ref|| <= tol * || |A| |x| ||: the scale of FP32 accumulation error
+    (for outputs of very few rows, where ||y|| itself may be small because of
+    cancellation inside a row)."""
+    scale = float(np.linalg.norm(abs_ref))
+    err = float(np.linalg.norm(got - ref))
+    assert err <= TOL[storage] * max(scale, 1e-300), (
+        f"{what}: ||err|| = {err:.3e} > {TOL[storage]:g} * || |A||x| || = {TOL[storage] * scale:.3e}")

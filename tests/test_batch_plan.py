@@ -1,0 +1,75 @@
+"""lak_batch_plan is host-only: its work table (unit counts, prefix offsets,
+per-instance vector-width decisions) is checked here without a GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def nat():
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    from paper_1409_0669_gb300 import _native
+    _native.load()
+    return _native
+
+
+def plan(nat, op, storage, descs, cfg=None):
+    lib = nat.load()
+    arr = (type(descs[0]) * len(descs))(*descs)
+    info = nat.BatchInfo()
+    cptr = ctypes.byref(cfg) if cfg is not None else None
+    assert lib.lak_batch_plan(nat.OPS[op], nat.DTYPES[storage], arr, len(descs), cptr, None, 0,
+                              ctypes.byref(info)) == 0
+    buf = (ctypes.c_uint8 * info.table_bytes)()
+    assert lib.lak_batch_plan(nat.OPS[op], nat.DTYPES[storage], arr, len(descs), cptr, buf,
+                              info.table_bytes, ctypes.byref(info)) == 0
+    raw = bytes(buf)
+    offs = np.frombuffer(raw[64:64 + 8 * (len(descs) + 1)], dtype=np.int64)
+    return info, offs, raw
+
+
+def test_axpy_units_and_offsets(nat):
+    cfg = nat.LakCfg(512, 0, 16, 0)          # unit = 512 threads * 16 * 4 passes = 32768
+    sizes = [0, 1, 32768, 32769, 100000]
+    descs = [nat.AxpyDesc(0x1000 * (i + 1) * 256, 0x2000 * (i + 1) * 256, 0x3000 * (i + 1) * 256,
+                          n, 0.5) for i, n in enumerate(sizes)]
+    info, offs, _ = plan(nat, "axpy", "f32", descs, cfg)
+    assert info.unit_elems == 32768
+    assert list(offs) == [0, 0, 1, 2, 4, 8]
+    assert info.total_units == 8 and info.workspace_bytes == 0
+
+
+def test_dot_empty_instances_still_get_a_unit(nat):
+    cfg = nat.LakCfg(256, 0, 4, 0)           # unit = 4096
+    descs = [nat.DotDesc(8 * (i + 1), 256 * (i + 1), 512 * (i + 1), n)
+             for i, n in enumerate([0, 4096, 4097, 0])]
+    info, offs, _ = plan(nat, "dot", "f32", descs, cfg)
+    assert list(offs) == [0, 1, 2, 4, 5]
+    assert info.workspace_bytes == 65536 + 8 * 5
+
+
+def test_gemv_rows_per_unit_and_spmv_units(nat):
+    cfg = nat.LakCfg(128, 0, 8, 0)           # unit = 4096 entries
+    g = [nat.GemvDesc(256, 512, 768, m, n, max(n, 1)) for m, n in ((100, 64), (10, 4096), (3, 10000),
+                                                             (0, 5), (7, 0))]
+    info, offs, _ = plan(nat, "gemv_row", "f32", g, cfg)
+    # rows per unit: ceil(4096/64)=64 -> 2 units; 1 row -> 10; 1 row -> 3; 0; n=0: all 7 rows -> 1
+    assert list(offs) == [0, 2, 12, 15, 15, 16]
+    c = [nat.CsrDesc(256, 512, 768, 1024, 1280, m, m, 5 * m) for m in (1, 64, 65, 1000)]
+    info, offs, _ = plan(nat, "spmv", "f32", c, nat.LakCfg(64, 0, 4, 0))
+    assert list(offs) == [0, 1, 2, 4, 20]
+
+
+def test_plan_rejects_bad_input(nat):
+    lib = nat.load()
+    info = nat.BatchInfo()
+    d = (nat.AxpyDesc * 1)(nat.AxpyDesc(0, 0, 0, -5, 1.0))
+    assert lib.lak_batch_plan(nat.OPS["axpy"], 0, d, 1, None, None, 0, ctypes.byref(info)) == -1
+    assert lib.lak_batch_plan(nat.OPS["copy"], 0, d, 1, None, None, 0, ctypes.byref(info)) == -1
+    assert lib.lak_batch_plan(nat.OPS["axpy"], 9, d, 1, None, None, 0, ctypes.byref(info)) == -2
+    many = (nat.DotDesc * 20000)()
+    assert lib.lak_batch_plan(nat.OPS["dot"], 0, many, 20000, None, None, 0,
+                              ctypes.byref(info)) == -1
+    assert "dot instances" in nat.last_error()

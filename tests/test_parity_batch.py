@@ -1,0 +1,144 @@
+"""Batched persistent launches against the FP64 oracle and the single-instance
+kernels: uneven instance sizes (log-uniform, with empty and one-element
+instances and misaligned slices), every batched op, and replay from a CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from checks import assert_dot, assert_normwise, assert_normwise_scaled, host
+
+pytestmark = pytest.mark.gpu
+
+
+def lak():
+    import paper_1409_0669_gb300 as m
+    return m
+
+
+def B():
+    from paper_1409_0669_gb300 import batch
+    return batch
+
+
+def sizes(count, lo, hi, seed, extra=(0, 1, 2, 3)):
+    s = list(synth.log_uniform_ints(count, lo, hi, seed))
+    return list(extra) + s
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+def test_axpy_batch_matches_single_calls(storage):
+    ns = sizes(300, 1, 200_000, 1)
+    dt = synth.torch_dtype(storage)
+    ys = [synth.uniform(n + 1, 10 + i, storage).cuda()[1:] if i % 7 == 0 else
+          synth.uniform(n, 10 + i, storage).cuda() for i, n in enumerate(ns)]
+    zs = [synth.uniform(n, 5000 + i, storage).cuda() for i, n in enumerate(ns)]
+    xs = [torch.empty(n, dtype=dt, device="cuda") for n in ns]
+    alphas = [0.5 if i % 2 else -1.25 for i in range(len(ns))]
+    b = B().axpy_batch(xs, ys, zs, alphas)
+    b.run()
+    torch.cuda.synchronize()
+    for x, y, z, a in zip(xs, ys, zs, alphas):
+        ref = torch.empty_like(x)
+        lak().vec_axpy(ref, y, z, a)
+        torch.cuda.synchronize()
+        assert torch.equal(x, ref)              # elementwise: identical bits
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_dot_batch_vs_oracle(storage):
+    ns = sizes(400, 1, 300_000, 2)
+    xs = [synth.uniform(n, 20 + i, storage).cuda() for i, n in enumerate(ns)]
+    ys = [synth.uniform(n, 9000 + i, storage).cuda() for i, n in enumerate(ns)]
+    odt = torch.float64 if storage == "f64" else torch.float32
+    out = torch.full((len(ns),), float("nan"), dtype=odt, device="cuda")
+    outs = [out[i:i + 1] for i in range(len(ns))]
+    b = B().dot_batch(xs, ys, outs)
+    for rep in range(3):                    # the arrival counters are reused
+        b.run()
+        torch.cuda.synchronize()
+        got = out.cpu().double().numpy()
+        for i, (x, y) in enumerate(zip(xs, ys)):
+            assert_dot(got[i], oracle.dot(x.cpu(), y.cpu()), host(x), host(y), storage,
+                       f"instance {i} (n={ns[i]}) rep {rep}")
+    assert torch.all(b.workspace[:65536] == 0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_gemv_batch_vs_oracle(storage):
+    ms = sizes(80, 1, 700, 3, extra=(1, 5, 0))
+    ns = sizes(80, 1, 700, 4, extra=(1, 0, 9))
+    dt = synth.torch_dtype(storage)
+    As, xs, ys, fulls = [], [], [], []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        pad = 3 if i % 5 == 0 else 0
+        full = synth.normal((m, n + pad), 30 + i, storage).cuda()
+        fulls.append(full)
+        As.append(full[:, :n])
+        xs.append(synth.uniform(n, 40 + i, storage).cuda())
+        ys.append(torch.full((m,), float("nan"), dtype=dt, device="cuda"))
+    b = B().gemv_batch(As, xs, ys)
+    b.run()
+    torch.cuda.synchronize()
+    for i, (A, x, y) in enumerate(zip(As, xs, ys)):
+        m, n = A.shape
+        if m == 0:
+            continue
+        if n == 0:
+            assert torch.all(y == 0)
+            continue
+        lda = fulls[i].shape[1]
+        flat = fulls[i].reshape(-1).cpu()
+        ref = oracle.gemv(flat, x.cpu(), m, n, lda, "row")
+        abs_ref = oracle.gemv(np.nan_to_num(np.abs(oracle.widen(flat))), np.abs(host(x)), m, n,
+                              lda, "row")
+        assert_normwise_scaled(host(y), ref, abs_ref, storage, f"instance {i} {m}x{n}")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_spmv_batch_vs_oracle(storage):
+    csrs, xs, ys, refs = [], [], [], []
+    rows = sizes(24, 1000, 20_000, 5, extra=(1, 31, 33))
+    for i, m in enumerate(rows):
+        if i == 3:
+            rp, ci, v = synth.laplacian_2d(64, storage)
+            m = 64 * 64
+        elif i == 4:
+            rp, ci, v = synth.random_csr(m, m, 60 + i, storage, 0, 40, 0.3)
+        else:
+            rp, ci, v = synth.banded_random_csr(m, 60 + i, 5, 64, storage)
+        x = synth.uniform(m, 70 + i, storage)
+        csrs.append((rp.cuda(), ci.cuda(), v.cuda(), m))
+        xs.append(x.cuda())
+        ys.append(torch.full((m,), float("nan"), dtype=v.dtype, device="cuda"))
+        refs.append(oracle.csr_spmv(rp, ci, v, x))
+    b = B().spmv_batch(csrs, xs, ys)
+    b.run()
+    torch.cuda.synchronize()
+    for i, (y, r) in enumerate(zip(ys, refs)):
+        assert_normwise(host(y), r, storage, f"instance {i}")
+
+
+def test_batch_replays_from_cuda_graph():
+    ns = sizes(64, 100, 50_000, 6)
+    xs = [synth.uniform(n, 80 + i, "f32").cuda() for i, n in enumerate(ns)]
+    ys = [synth.uniform(n, 180 + i, "f32").cuda() for i, n in enumerate(ns)]
+    out = torch.zeros(len(ns), device="cuda")
+    b = B().dot_batch(xs, ys, [out[i:i + 1] for i in range(len(ns))])
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(s)                              # warm: loads the kernels before capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    first = out.clone()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    for _ in range(5):
+        out.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, first)
