@@ -456,6 +456,125 @@ def roofline_of(it, ms, hbm_peak, hbm_kind, fp64_peak):
     return (alu, hbm) if alu["frac"] > hbm["frac"] else (hbm, alu)
 
 
+def run_batched(device, reps=10, count=4096, seed=4000):
+    """4096 uneven instances per family, each family in ONE persistent launch
+    (block, grid and vector width from the autotuned defaults), all families
+    captured in one CUDA graph.  Compared with 4096 separate launches per
+    family (issued from the host) and with one CUDA graph of those separate
+    launches.  Instance sizes: vectors n ~ log-uniform 256..1M (axpy, dot);
+    dense GEMV m, n ~ log-uniform 64..4096; CSR blocks of 1k..200k rows with
+    5..64 entries per row (square, random columns)."""
+    import ctypes
+
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300 import _native
+    from paper_1409_0669_gb300 import batch as B
+
+    lib = _native.load()
+    dev = device
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    code = _native.DTYPES["f32"]
+    fams = {}
+
+    ns = synth.log_uniform_ints(count, 256, 1_048_576, seed)
+    buf_len = int(sum((int(n) + 63) // 64 * 64 for n in ns))
+    ybuf = synth.device_uniform_(torch.empty(buf_len, device=dev), seed + 1)
+    zbuf = synth.device_uniform_(torch.empty(buf_len, device=dev), seed + 2)
+    xbuf = torch.zeros(buf_len, device=dev)
+    ys, zs, xs, o = [], [], [], 0
+    for n in ns:
+        n = int(n)
+        ys.append(ybuf[o:o + n]); zs.append(zbuf[o:o + n]); xs.append(xbuf[o:o + n])
+        o += (n + 63) // 64 * 64
+    outs = torch.zeros(count, device=dev)
+    wsd = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+    fams["axpy"] = (B.axpy_batch(xs, ys, zs, [0.5] * count),
+                    [(lib.vec_axpy, (x.data_ptr(), y.data_ptr(), z.data_ptr(), 0.5, x.numel(),
+                                     code, None, sh)) for x, y, z in zip(xs, ys, zs)],
+                    int(sum(3 * 4 * int(n) for n in ns)))
+    fams["dot"] = (B.dot_batch(ys, zs, [outs[i:i + 1] for i in range(count)]),
+                   [(lib.vec_dot, (outs[i:i + 1].data_ptr(), y.data_ptr(), z.data_ptr(),
+                                   y.numel(), code, wsd.data_ptr(), wsd.numel(), None, sh))
+                    for i, (y, z) in enumerate(zip(ys, zs))],
+                   int(sum(2 * 4 * int(n) for n in ns)))
+
+    ms = synth.log_uniform_ints(count, 64, 4096, seed + 3)
+    nn = synth.log_uniform_ints(count, 64, 4096, seed + 4)
+    As, gx, gy = [], [], []
+    for i, (m, n) in enumerate(zip(ms, nn)):
+        m, n = int(m), int(n)
+        As.append(synth.device_normal_(torch.empty(m, n, device=dev), seed + 10 + i))
+        gx.append(synth.device_uniform_(torch.empty(n, device=dev), seed + 20000 + i))
+        gy.append(torch.zeros(m, device=dev))
+    fams["gemv"] = (B.gemv_batch(As, gx, gy),
+                    [(lib.dense_gemv, (y.data_ptr(), A.data_ptr(), x.data_ptr(), A.shape[0],
+                                       A.shape[1], A.shape[1], 0, code, None, 0, None, sh))
+                     for A, x, y in zip(As, gx, gy)],
+                    int(sum((int(m) * int(n) + int(m) + int(n)) * 4 for m, n in zip(ms, nn))))
+
+    rows = synth.log_uniform_ints(count, 1000, 200_000, seed + 5)
+    csrs, cx, cy, cbytes = [], [], [], 0
+    for i, m in enumerate(rows):
+        m = int(m)
+        rp, ci, v = synth.device_csr_block_(m, seed + 40000 + i, 5, 64, torch.float32, dev)
+        csrs.append((rp, ci, v, m))
+        cx.append(synth.device_uniform_(torch.empty(m, device=dev), seed + 60000 + i))
+        cy.append(torch.zeros(m, device=dev))
+        cbytes += v.numel() * 8 + (m + 1) * 4 + 2 * m * 4
+    fams["spmv"] = (B.spmv_batch(csrs, cx, cy),
+                    [(lib.csr_spmv, (y.data_ptr(), rp.data_ptr(), ci.data_ptr(), v.data_ptr(),
+                                     x.data_ptr(), m, m, v.numel(), code, None, sh))
+                     for (rp, ci, v, m), x, y in zip(csrs, cx, cy)],
+                    int(cbytes))
+    torch.cuda.synchronize()
+
+    def separate(calls):
+        for fn, a in calls:
+            st = fn(*a)
+            if st != 0:
+                _native.check("separate launch", st)
+
+    report = {"instances_per_family": count, "dtype": "f32",
+              "sizes": "vectors log-uniform 256..1M; GEMV m,n log-uniform 64..4096; "
+                       "CSR 1k..200k rows x 5..64 nnz/row"}
+    for name, (bt, calls, nbytes) in fams.items():
+        for _ in range(3):
+            bt.run()
+        separate(calls)
+        torch.cuda.synchronize()
+        t_b = _median_ms(bt.run, reps)
+        t_s = _median_ms(lambda: separate(calls), max(3, reps // 3))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            separate_graph_calls = [(fn, a[:-1] + (torch.cuda.current_stream().cuda_stream,))
+                                    for fn, a in calls]
+            separate(separate_graph_calls)
+        t_g = _median_ms(g.replay, reps)
+        del g
+        report[name] = {"bytes": nbytes, "units": bt.total_units,
+                        "us_batched": round(t_b * 1e3, 1),
+                        "GBs_batched": round(nbytes / (t_b * 1e-3) / 1e9, 1),
+                        "us_separate_launches": round(t_s * 1e3, 1),
+                        "us_graph_of_separate": round(t_g * 1e3, 1),
+                        "speedup_vs_separate": round(t_s / t_b, 2),
+                        "speedup_vs_graph_of_separate": round(t_g / t_b, 2)}
+    # every family's persistent launch in one CUDA graph
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for bt, _, _ in fams.values():
+            bt.run()
+    t_all = _median_ms(g.replay, reps)
+    tot = sum(nb for _, _, nb in fams.values())
+    report["all_families_one_graph"] = {"bytes": tot, "us": round(t_all * 1e3, 1),
+                                        "GBs": round(tot / (t_all * 1e-3) / 1e9, 1)}
+    del ctypes
+    return report
+
+
 def recorded_traffic(path, name):
     """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
     when there is no record or the kernel's source changed since the capture."""
@@ -729,6 +848,9 @@ def run_gb300(args):
     precision = None
     if not args.no_precision and not args.only and rank == 0:
         precision = run_precision(device)
+    batched = None
+    if not args.no_batched and not args.only and rank == 0:
+        batched = run_batched(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -751,6 +873,8 @@ def run_gb300(args):
         line["cpu_baseline"] = cpu
     if precision is not None:
         line["precision"] = precision
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -817,6 +941,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the BF16/FP16-storage and compensated-dot report")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (4096 uneven instances per family) report")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")

@@ -1,19 +1,21 @@
 // Batched operations: many independent instances of uneven sizes in one
 // persistent launch.
 //
-// lak_batch_plan (host, no CUDA call) splits every instance into work units of
-// about the same size -- `unit_elems` elements of a vector, a run of rows of a
-// dense matrix with about as many entries, or one block's worth of 32-row CSR
-// blocks -- and writes a table: a header, the exclusive prefix of units per
+// lak_batch_plan (host, no CUDA call) splits every instance into work units --
+// `unit_elems` elements of a vector or a run of rows of a dense matrix with
+// about as many entries (about 256 KB of one operand), or one block's rows of a
+// CSR matrix -- and writes a table: a header, the exclusive prefix of units per
 // instance, and per-instance items (the caller's descriptor plus the launch
 // details the plan chose).  lak_batch_run launches one persistent grid over
 // all units; a block maps its unit to an instance with a binary search over
 // the prefix (a few L1-resident loads) and runs the same inner loops as the
-// single-instance kernels.  Batched dot products finish per instance with the
+// single-instance kernels (dense rows with a lane group per row sized from the
+// row length; CSR rows with the warp-segmented body).  Batched dot products finish per instance with the
 // last-arriving-unit combine (an arrival counter per instance in the workspace
 // counter area), in unit order, so results are deterministic.
 #include <cstddef>
 
+#include "gemv_row.cuh"
 #include "lak_internal.cuh"
 #include "spmv_seg.cuh"
 
@@ -28,6 +30,8 @@ struct BatchHead {
     int32_t dtype;
     int32_t vec;
     int32_t block;
+    int32_t inc;
+    int32_t pad;
 };
 
 struct AxpyItem {
@@ -46,11 +50,11 @@ struct GemvItem {
     lak_gemv_desc d;
     int64_t rows_per_unit;
     int32_t vec_ok;
-    int32_t pad;
+    int32_t group;           // lanes per row (power of two <= 32)
 };
 struct CsrItem {
     lak_csr_desc d;
-    int64_t units;
+    int64_t rows_per_unit;   // a multiple of the block's rows (32 per warp)
     int32_t vec_ok;
     int32_t pad;
 };
@@ -90,13 +94,28 @@ __device__ __forceinline__ int64_t find_instance(const int64_t *offs, int64_t co
     return lo;
 }
 
+// The order in which a block takes units follows the configuration's
+// increment type (Sec. 2): global = grid-stride (the blocks resident on one SM
+// take consecutive units, usually of one instance, and share its re-read
+// operands in L1); local = each block walks one contiguous range of units.
+struct UnitRange {
+    int64_t begin, end, step;
+};
+__device__ __forceinline__ UnitRange unit_range(int64_t total, int inc) {
+    if (inc == LAK_INC_GLOBAL) return {(int64_t)blockIdx.x, total, (int64_t)gridDim.x};
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t b = (int64_t)blockIdx.x * per;
+    return {b, b + per < total ? b + per : total, 1};
+}
+
 template <typename T, int V>
 __global__ void __launch_bounds__(512)
 axpy_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                   const AxpyItem *__restrict__ items) {
     using A = typename Acc<T>::type;
     const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const UnitRange ur = unit_range(total, head->inc);
+    for (int64_t u = ur.begin; u < ur.end; u += ur.step) {
         const int64_t i = find_instance(offs, count, u);
         const AxpyItem it = items[i];
         T *x = static_cast<T *>(it.d.x);
@@ -133,7 +152,8 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
     __shared__ double wsum[32];
     const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const UnitRange ur = unit_range(total, head->inc);
+    for (int64_t u = ur.begin; u < ur.end; u += ur.step) {
         const int64_t i = find_instance(offs, count, u);
         const DotItem it = items[i];
         const T *x = static_cast<const T *>(it.d.x);
@@ -197,43 +217,32 @@ gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
     using A = typename Acc<T>::type;
     const int64_t count = head->count, total = head->total_units;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const UnitRange ur = unit_range(total, head->inc);
+    for (int64_t u = ur.begin; u < ur.end; u += ur.step) {
         const int64_t i = find_instance(offs, count, u);
         const GemvItem it = items[i];
         const T *Am = static_cast<const T *>(it.d.A);
         const T *x = static_cast<const T *>(it.d.x);
         T *y = static_cast<T *>(it.d.y);
         const int64_t n = it.d.n, lda = it.d.lda;
+        const int G = it.group;                     // lanes per row
+        const int rpw = 32 / G;                     // rows per warp at a time
+        const int lg = lane % G;
         const int64_t r0 = (u - __ldg(offs + i)) * it.rows_per_unit;
         const int64_t r1 = r0 + it.rows_per_unit < it.d.m ? r0 + it.rows_per_unit : it.d.m;
-        for (int64_t row = r0 + warp; row < r1; row += nwarps) {   // warp-uniform
-            const T *Ar = Am + row * lda;
+        for (int64_t rb = r0 + (int64_t)warp * rpw; rb < r1; rb += (int64_t)nwarps * rpw) {
+            const int64_t row = rb + lane / G;       // warp-uniform trip count
             A acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = A(0);
-            int64_t k = 0;
-            if (it.vec_ok) {
-                const int64_t nch = n / V;
-#pragma unroll 4
-                for (int64_t c = lane; c < nch; c += 32) {
-                    Pack<T, V> pa, px;
-                    load_pack<T, V, STREAM>(pa, Ar + c * V);
-                    load_pack<T, V, CACHED>(px, x + c * V);
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        acc[v] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[v]);
-                }
-                k = nch * V;
-            }
-            for (int64_t j = k + lane; j < n; j += 32)
-                acc[0] = fma_acc(widen(Ar[j]), widen(ld_cached(x + j)), acc[0]);
+            if (row < r1) row_group_dot<T, V>(acc, Am + row * lda, x, n, lg, G);
 #pragma unroll
             for (int w = 1; w < V; w <<= 1) {
 #pragma unroll
                 for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
             }
-            const A s = group_sum(acc[0], 32);
-            if (lane == 0) y[row] = narrow<T>(s);
+            const A s = group_sum(acc[0], G);
+            if (lg == 0 && row < r1) y[row] = narrow<T>(s);
         }
     }
 }
@@ -247,22 +256,27 @@ spmv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
     __shared__ Ac racc_all[16][32];
     const int64_t count = head->count, total = head->total_units;
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const UnitRange ur = unit_range(total, head->inc);
+    for (int64_t u = ur.begin; u < ur.end; u += ur.step) {
         const int64_t i = find_instance(offs, count, u);
         const CsrItem it = items[i];
-        const int64_t b = (u - __ldg(offs + i)) * wpb + warp;    // this warp's 32-row block
-        if (b * 32 >= it.d.m) continue;                             // warp-uniform
+        const int64_t nb = (it.d.m + 31) / 32;                      // 32-row blocks
+        const int64_t bpu = it.rows_per_unit / 32;                   // per unit
+        const int64_t b0 = (u - __ldg(offs + i)) * bpu;
+        const int64_t b1 = b0 + bpu < nb ? b0 + bpu : nb;
         const int64_t nnz = __ldg(it.d.row_ptr + it.d.m);
-        if (it.vec_ok)
-            seg_rows32<T, U, true>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
-                                   static_cast<const T *>(it.d.vals),
-                                   static_cast<const T *>(it.d.x), it.d.m, nnz, b, rs_all[warp],
-                                   racc_all[warp]);
-        else
-            seg_rows32<T, U, false>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
-                                    static_cast<const T *>(it.d.vals),
-                                    static_cast<const T *>(it.d.x), it.d.m, nnz, b, rs_all[warp],
-                                    racc_all[warp]);
+        for (int64_t b = b0 + warp; b < b1; b += wpb) {              // warp-uniform
+            if (it.vec_ok)
+                seg_rows32<T, U, true>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
+                                       static_cast<const T *>(it.d.vals),
+                                       static_cast<const T *>(it.d.x), it.d.m, nnz, b,
+                                       rs_all[warp], racc_all[warp]);
+            else
+                seg_rows32<T, U, false>(static_cast<T *>(it.d.y), it.d.row_ptr, it.d.col_idx,
+                                        static_cast<const T *>(it.d.vals),
+                                        static_cast<const T *>(it.d.x), it.d.m, nnz, b,
+                                        rs_all[warp], racc_all[warp]);
+        }
     }
 }
 
@@ -338,7 +352,14 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
     if (op == LAK_OP_SPMV) vec = vec < 4 ? 4 : (vec > 8 ? 8 : vec);   // seg rows: 4..8 entries
     const int es = esize(dtype);
     const int w = access_bytes(vec, es);
-    const int64_t ue = (int64_t)c.block * vec * 4;                  // ~4 passes per thread
+    // work units of about 256 KB of one operand: vectors and GEMV entries in
+    // multiples of one pass of the block; CSR rows in multiples of the block's
+    // rows (32 per warp), sized from the instance's mean row length
+    const int64_t pass = (int64_t)c.block * vec;
+    const int64_t ue = cdiv((int64_t)262144 / es, pass) * pass;
+    // CSR: one block's rows per unit (32 per warp); co-resident blocks take
+    // consecutive units of the same instance and share its x in L1
+    auto csr_rows_per_unit = [&](const lak_csr_desc &) { return (int64_t)c.block; };
     const size_t isz = item_size(op);
     const size_t need = items_offset(count) + isz * (size_t)count;
 
@@ -371,7 +392,7 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
             const lak_csr_desc &d = static_cast<const lak_csr_desc *>(host_descs)[i];
             if (d.m < 0 || d.n < 0 || d.nnz < 0 || d.nnz > 0x7fffffffLL)
                 return fail(LAK_EINVAL, "lak_batch_plan: instance %lld: bad sizes", (long long)i);
-            units = cdiv(d.m, c.block);                 // (block/32) 32-row blocks per unit
+            units = cdiv(d.m, csr_rows_per_unit(d));
             break;
         }
         default: break;
@@ -401,6 +422,7 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
     h->dtype = (int32_t)dtype;
     h->vec = vec;
     h->block = c.block;
+    h->inc = c.increment;
     int64_t *offs = reinterpret_cast<int64_t *>(t + kHeadBytes);
     char *items = t + items_offset(count);
     int64_t acc = 0;
@@ -434,6 +456,13 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
             const int64_t rpu = d.n > 0 ? (cdiv(ue, d.n) < d.m ? cdiv(ue, d.n) : d.m) : d.m;
             it.rows_per_unit = rpu > 0 ? rpu : 1;
             it.vec_ok = aligned_to(d.A, w) && aligned_to(d.x, w) && (d.lda * es) % w == 0;
+            // lanes per row: at least one 128-byte line of the row per warp
+            // instruction (DRAM fetches whole lines), more while every lane
+            // still sees about 4 vector groups
+            int G = 1;
+            while (G < 32 && (int64_t)G * vec * es < 128) G *= 2;
+            while (G < 32 && (int64_t)G * 2 * vec * 4 <= d.n) G *= 2;
+            it.group = G;
             memcpy(items + isz * i, &it, sizeof it);
             acc += d.m > 0 ? cdiv(d.m, it.rows_per_unit) : 0;
             break;
@@ -442,10 +471,10 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
             const lak_csr_desc &d = static_cast<const lak_csr_desc *>(host_descs)[i];
             CsrItem it{};
             it.d = d;
-            it.units = cdiv(d.m, c.block);
+            it.rows_per_unit = csr_rows_per_unit(d);
             it.vec_ok = aligned_to(d.col_idx, 16) && aligned_to(d.vals, 16);
             memcpy(items + isz * i, &it, sizeof it);
-            acc += it.units;
+            acc += cdiv(d.m, it.rows_per_unit);
             break;
         }
         default: break;

@@ -4,9 +4,11 @@
 //
 // Row-major: a group of G threads (G a power of two, from 1 up to the whole
 // block) owns one row; each thread reads V consecutive matrix entries per step
-// with wide streamed loads and the matching V entries of x with cached loads
-// (x is re-read by every row, so it lives in L1/L2), then the group reduces
-// with shuffles (and shared memory across warps when G > 32).  G grows with
+// with wide streamed loads (after a short per-row head that brings the row to
+// the access width, so any leading dimension takes the wide path) and the
+// matching V entries of x with cached loads (x is re-read by every row, so it
+// lives in L1/L2), then the group reduces with shuffles (and shared memory
+// across warps when G > 32).  G grows with
 // the row length, so long rows use a whole block -- the paper's one
 // work-group per row -- and short rows pack several rows per warp.
 //
@@ -18,6 +20,7 @@
 // each split stores its partial tile in the workspace and the last split to
 // arrive at a row tile adds the partials in split order -- deterministic and
 // free of floating-point atomics.
+#include "gemv_row.cuh"
 #include "lak_internal.cuh"
 
 namespace lak {
@@ -32,8 +35,6 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
     const int R = blockDim.x / G;                  // rows per block step
     const int grp = threadIdx.x / G;
     const int lg = threadIdx.x % G;
-    const int64_t nch = n / V;                     // full V-groups per row
-    const int ntail = (int)(n - nch * V);
 
     int64_t row0, row_end, step;
     if (inc == LAK_INC_GLOBAL) {
@@ -52,21 +53,7 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         Ac acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = Ac(0);
-        if (row < row_end) {
-            const T *Ar = A + row * lda;
-#pragma unroll 4
-            for (int64_t c = lg; c < nch; c += G) {
-                Pack<T, V> pa, px;
-                load_pack<T, V, STREAM>(pa, Ar + c * V);
-                load_pack<T, V, CACHED>(px, x + c * V);
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    acc[v] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[v]);
-            }
-            if (lg < ntail)
-                acc[0] = fma_acc(widen(Ar[nch * V + lg]), widen(ld_cached(x + nch * V + lg)),
-                                 acc[0]);
-        }
+        if (row < row_end) row_group_dot<T, V>(acc, A + row * lda, x, n, lg, G);
 #pragma unroll
         for (int w = 1; w < V; w <<= 1) {
 #pragma unroll

@@ -207,17 +207,15 @@ lak_status plan_gemv_row(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const 
     if (!di) return LAK_ECUDA;
     lak_cfg c = base_cfg(LAK_OP_GEMV_ROW, dt, cfg);
     const int es = esize(dt);
-    int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_ROW, dt).vec;
-    // every row start and x must sit on the access width
-    while (vec > 1) {
-        const int w = access_bytes(vec, es);
-        const bool ok = (!A || (uintptr_t)A % w == 0) && (!x || (uintptr_t)x % w == 0) &&
-                        ((lda * es) % w == 0);
-        if (ok) break;
-        vec >>= 1;
-    }
+    const int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_ROW, dt).vec;
+    (void)A;   // rows are brought to the access width in the kernel (per-row head)
+    (void)x;
+    (void)lda;
     const int64_t nch = n / vec;
     int G = pow2_floor(nch / 4 > 0 ? nch / 4 : 1);
+    // at least one 128-byte line of a row per group access: DRAM fetches whole
+    // lines, so narrower groups would waste part of every fetch
+    while (G < 32 && (int64_t)G * vec * es < 128) G *= 2;
     const int bp = block_pow2(c.block);
     if (G > bp) G = bp;
     const int R = c.block / G;

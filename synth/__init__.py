@@ -261,3 +261,17 @@ def device_mixed_magnitude_(out: torch.Tensor, seed: int, lo_exp: float = -4.0,
     sign = torch.randint(0, 2, out.shape, generator=g, device=out.device).to(torch.float64) * 2 - 1
     out.copy_(sign * torch.pow(10.0, e))
     return out
+
+
+def device_csr_block_(m: int, seed: int, min_len: int, max_len: int, dtype, device):
+    """A square m x m CSR block generated on the device: row lengths uniform in
+    [min_len, max_len], columns uniform in [0, m) (unsorted, repeats allowed --
+    CSR sums them), values N(0, 1).  Returns (row_ptr int32, col_idx int32, vals)."""
+    g = torch.Generator(device=device).manual_seed(seed)
+    lens = torch.randint(min_len, max_len + 1, (m,), generator=g, device=device, dtype=torch.int32)
+    rp = torch.zeros(m + 1, dtype=torch.int32, device=device)
+    torch.cumsum(lens, 0, out=rp[1:])
+    nnz = int(rp[-1].item())
+    ci = torch.randint(0, m, (nnz,), generator=g, device=device, dtype=torch.int32)
+    v = torch.empty(nnz, dtype=torch.float32, device=device).normal_(0.0, 1.0, generator=g)
+    return rp, ci, v.to(dtype)

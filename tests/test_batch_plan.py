@@ -31,32 +31,33 @@ def plan(nat, op, storage, descs, cfg=None):
 
 
 def test_axpy_units_and_offsets(nat):
-    cfg = nat.LakCfg(512, 0, 16, 0)          # unit = 512 threads * 16 * 4 passes = 32768
-    sizes = [0, 1, 32768, 32769, 100000]
+    cfg = nat.LakCfg(512, 0, 16, 0)          # unit = 256 KB of FP32 = 65536 elements
+    sizes = [0, 1, 65536, 65537, 200000]
     descs = [nat.AxpyDesc(0x1000 * (i + 1) * 256, 0x2000 * (i + 1) * 256, 0x3000 * (i + 1) * 256,
                           n, 0.5) for i, n in enumerate(sizes)]
     info, offs, _ = plan(nat, "axpy", "f32", descs, cfg)
-    assert info.unit_elems == 32768
+    assert info.unit_elems == 65536
     assert list(offs) == [0, 0, 1, 2, 4, 8]
     assert info.total_units == 8 and info.workspace_bytes == 0
 
 
 def test_dot_empty_instances_still_get_a_unit(nat):
-    cfg = nat.LakCfg(256, 0, 4, 0)           # unit = 4096
+    cfg = nat.LakCfg(256, 0, 4, 0)           # unit = 65536 FP32 elements
     descs = [nat.DotDesc(8 * (i + 1), 256 * (i + 1), 512 * (i + 1), n)
-             for i, n in enumerate([0, 4096, 4097, 0])]
+             for i, n in enumerate([0, 65536, 65537, 0])]
     info, offs, _ = plan(nat, "dot", "f32", descs, cfg)
     assert list(offs) == [0, 1, 2, 4, 5]
     assert info.workspace_bytes == 65536 + 8 * 5
 
 
 def test_gemv_rows_per_unit_and_spmv_units(nat):
-    cfg = nat.LakCfg(128, 0, 8, 0)           # unit = 4096 entries
-    g = [nat.GemvDesc(256, 512, 768, m, n, max(n, 1)) for m, n in ((100, 64), (10, 4096), (3, 10000),
-                                                             (0, 5), (7, 0))]
+    cfg = nat.LakCfg(128, 0, 8, 0)           # unit = 65536 entries
+    g = [nat.GemvDesc(256, 512, 768, m, n, max(n, 1))
+         for m, n in ((2000, 64), (40, 4096), (3, 100000), (0, 5), (7, 0))]
     info, offs, _ = plan(nat, "gemv_row", "f32", g, cfg)
-    # rows per unit: ceil(4096/64)=64 -> 2 units; 1 row -> 10; 1 row -> 3; 0; n=0: all 7 rows -> 1
-    assert list(offs) == [0, 2, 12, 15, 15, 16]
+    # rows per unit: 1024 -> 2 units; 16 -> 3 units; 1 -> 3 units; none; n = 0: all 7 -> 1
+    assert list(offs) == [0, 2, 5, 8, 8, 9]
+    # CSR: one block's rows (64) per unit
     c = [nat.CsrDesc(256, 512, 768, 1024, 1280, m, m, 5 * m) for m in (1, 64, 65, 1000)]
     info, offs, _ = plan(nat, "spmv", "f32", c, nat.LakCfg(64, 0, 4, 0))
     assert list(offs) == [0, 1, 2, 4, 20]
