@@ -271,6 +271,51 @@ LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_
                             void *stream);
 
 /* ------------------------------------------------------------------------
+ * Reverse-mode building blocks for the products above (an extension of this
+ * library; the paper studies forward operations only).  For y = A x:
+ * dA = dy x^T (dense_outer; on a CSR pattern csr_sampled_outer) and
+ * dx = A^T dy (dense_gemv on the same storage with the other layout; for CSR a
+ * csr_spmv on the transpose from csr_transpose, with the values brought into
+ * its order by vec_gather).  For s = <x, y>: dx = ds * y (vec_scale_dev, the
+ * scale read from device memory so that no host synchronisation is needed).
+ * ---------------------------------------------------------------------- */
+
+/* dA[i*ldd + j] = dy[i] * x[j] for i < m, j < n (ldd >= n); one product
+ * rounded once to the storage type. */
+LAK_API lak_status dense_outer(void *dA, const void *dy, const void *x, int64_t m, int64_t n,
+                               int64_t ldd, lak_dtype dtype, void *stream);
+
+/* dvals[k] = dy[i] * x[col_idx[k]] for every stored entry k of row i of an
+ * m-row CSR pattern with nnz entries (the gradient of the CSR product with
+ * respect to its values). */
+LAK_API lak_status csr_sampled_outer(void *dvals, const int32_t *row_ptr, const int32_t *col_idx,
+                                     const void *dy, const void *x, int64_t m, int64_t nnz,
+                                     lak_dtype dtype, void *stream);
+
+/* Workspace bytes csr_transpose needs for a matrix with n columns. */
+LAK_API size_t csr_transpose_workspace(int64_t n);
+
+/* The CSC form of an m-by-n CSR pattern: col_ptr (n+1), row_idx (nnz) and
+ * perm (nnz), perm[q] = the CSR position of the q-th CSC entry, entries of
+ * each column in increasing CSR position (the result of a stable counting
+ * sort; deterministic).  (col_ptr, row_idx) with values vals[perm] is A^T in
+ * CSR form.  Workspace: csr_transpose_workspace(n) bytes, 256-byte aligned, no
+ * initial contents required. */
+LAK_API lak_status csr_transpose(int32_t *col_ptr, int32_t *row_idx, int32_t *perm,
+                                 const int32_t *row_ptr, const int32_t *col_idx, int64_t m,
+                                 int64_t n, int64_t nnz, void *workspace, size_t ws_bytes,
+                                 void *stream);
+
+/* dst[i] = src[idx[i]] for i < n (a bit copy of elements of `dtype`). */
+LAK_API lak_status vec_gather(void *dst, const void *src, const int32_t *idx, int64_t n,
+                              lak_dtype dtype, void *stream);
+
+/* out[i] = alpha * v[i], alpha ONE DEVICE element: float for F32/BF16/F16,
+ * double for F64 (the type vec_dot writes). */
+LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, int64_t n,
+                                 lak_dtype dtype, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched operations: many independent instances of uneven sizes in one
  * persistent launch (an extension of this library; the paper runs one
  * operation at a time).

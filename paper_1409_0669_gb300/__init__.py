@@ -25,7 +25,8 @@ from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
 __all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
            "vec_dot_noalloc", "dense_gemv",
-           "dense_gemv_workspace", "csr_spmv", "resolve_cfg", "set_default_cfg", "Cfg",
+           "dense_gemv_workspace", "csr_spmv", "dense_outer", "csr_sampled_outer",
+           "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg", "Cfg",
            "LakError", "storage_of", "library_path"]
 
 _lib = _native.load()
@@ -307,3 +308,85 @@ def csr_spmv(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor, x
                        m, n, nnz, DTYPES[s], _cfg_ptr(cfg), _stream(stream))
     _native.check("csr_spmv", st)
     return y
+
+
+# ---- reverse-mode building blocks ---------------------------------------------------
+
+def dense_outer(dy: torch.Tensor, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+    """dA = dy x^T as an (m, n) row-major tensor."""
+    s = _same_storage(dy, x)
+    m, n = dy.numel(), x.numel()
+    if out is None:
+        out = torch.empty(m, n, dtype=dy.dtype, device=dy.device)
+    if out.dim() != 2 or out.shape != (m, n) or (n > 1 and out.stride(1) != 1):
+        raise ValueError("out must be an (m, n) tensor with unit stride along rows")
+    ldd = out.stride(0) if m > 1 else max(n, 1)
+    st = _lib.dense_outer(_dev_ptr(out, "out"), _vec_arg(dy, "dy"), _vec_arg(x, "x"), m, n, ldd,
+                          DTYPES[s], _stream(stream))
+    _native.check("dense_outer", st)
+    return out
+
+
+def csr_sampled_outer(row_ptr: torch.Tensor, col_idx: torch.Tensor, dy: torch.Tensor,
+                      x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                      stream=None) -> torch.Tensor:
+    """dvals[k] = dy[row(k)] * x[col(k)] on the CSR pattern."""
+    s = _same_storage(dy, x)
+    m = row_ptr.numel() - 1
+    nnz = col_idx.numel()
+    if out is None:
+        out = torch.empty(nnz, dtype=dy.dtype, device=dy.device)
+    st = _lib.csr_sampled_outer(_vec_arg(out, "out") if nnz else None, _vec_arg(row_ptr, "row_ptr"),
+                                _vec_arg(col_idx, "col_idx") if nnz else None, _vec_arg(dy, "dy"),
+                                _vec_arg(x, "x") if x.numel() else None, m, nnz, DTYPES[s],
+                                _stream(stream))
+    _native.check("csr_sampled_outer", st)
+    return out
+
+
+def csr_transpose(row_ptr: torch.Tensor, col_idx: torch.Tensor, n_cols: int, stream=None):
+    """(col_ptr, row_idx, perm) of the CSC form (int32 device tensors)."""
+    m = row_ptr.numel() - 1
+    nnz = col_idx.numel()
+    dev = row_ptr.device
+    col_ptr = torch.empty(n_cols + 1, dtype=torch.int32, device=dev)
+    row_idx = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    perm = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    ws_bytes = int(_lib.csr_transpose_workspace(int(n_cols)))
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    st = _lib.csr_transpose(col_ptr.data_ptr(), row_idx.data_ptr(), perm.data_ptr(),
+                            _vec_arg(row_ptr, "row_ptr"), _vec_arg(col_idx, "col_idx") if nnz else None,
+                            m, int(n_cols), nnz, ws.data_ptr(), ws.numel(), _stream(stream))
+    _native.check("csr_transpose", st)
+    return col_ptr, row_idx[:nnz], perm[:nnz]
+
+
+def vec_gather(src: torch.Tensor, idx: torch.Tensor, out: Optional[torch.Tensor] = None,
+               stream=None) -> torch.Tensor:
+    """out[i] = src[idx[i]] (idx int32)."""
+    s = storage_of(src)
+    n = idx.numel()
+    if out is None:
+        out = torch.empty(n, dtype=src.dtype, device=src.device)
+    st = _lib.vec_gather(_vec_arg(out, "out") if n else None, _vec_arg(src, "src") if src.numel() else None,
+                         _vec_arg(idx, "idx") if n else None, n, DTYPES[s], _stream(stream))
+    _native.check("vec_gather", st)
+    return out
+
+
+def vec_scale_dev(v: torch.Tensor, alpha: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """out = alpha * v with alpha a one-element device tensor (float32; float64
+    for FP64 storage)."""
+    s = storage_of(v)
+    adt = torch.float64 if s == "f64" else torch.float32
+    if alpha.dtype != adt or not alpha.is_cuda:
+        raise TypeError(f"alpha must be a CUDA {adt} tensor")
+    if out is None:
+        out = torch.empty_like(v)
+    n = v.numel()
+    st = _lib.vec_scale_dev(_vec_arg(out, "out") if n else None, _vec_arg(v, "v") if n else None,
+                            alpha.data_ptr(), n, DTYPES[s], _stream(stream))
+    _native.check("vec_scale_dev", st)
+    return out

@@ -25,7 +25,9 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
            "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
            "vec_dot_noalloc",
-           "dense_gemv_workspace", "dense_gemv", "csr_spmv", "lak_batch_plan", "lak_batch_run")
+           "dense_gemv_workspace", "dense_gemv", "csr_spmv", "dense_outer", "csr_sampled_outer",
+           "csr_transpose_workspace", "csr_transpose", "vec_gather", "vec_scale_dev",
+           "lak_batch_plan", "lak_batch_run")
 
 
 class LakCfg(ctypes.Structure):
@@ -94,6 +96,12 @@ _SIGNATURES = {
     "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
     "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
     "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
+    "dense_outer": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _P]),
+    "csr_sampled_outer": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I32, _P]),
+    "csr_transpose_workspace": (_SZ, [_I64]),
+    "csr_transpose": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P, _SZ, _P]),
+    "vec_gather": (_I32, [_P, _P, _P, _I64, _I32, _P]),
+    "vec_scale_dev": (_I32, [_P, _P, _P, _I64, _I32, _P]),
     "lak_batch_plan": (_I32, [_I32, _I32, _P, _I64, _CFGP, _P, _SZ, ctypes.POINTER(BatchInfo)]),
     "lak_batch_run": (_I32, [ctypes.POINTER(BatchInfo), _P, _P, _SZ, _P]),
 }

@@ -1,0 +1,128 @@
+"""Differentiation: autograd Functions whose forward and backward run in the
+library's kernels, checked by torch.autograd.gradcheck (central finite
+differences in FP64) and against reference gradients built from the FP64
+oracle; the CSR transpose against the oracle's stable counting sort."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from checks import assert_normwise, host
+
+pytestmark = pytest.mark.gpu
+
+
+def lak():
+    import paper_1409_0669_gb300 as m
+    return m
+
+
+def AG():
+    from paper_1409_0669_gb300 import autograd
+    return autograd
+
+
+def test_gradcheck_fp64_dense_csr_dot():
+    ag = AG()
+    A = synth.normal((32, 32), 1, "f64").cuda().requires_grad_()
+    x = synth.uniform(32, 2, "f64").cuda().requires_grad_()
+    assert torch.autograd.gradcheck(ag.gemv, (A, x), eps=1e-6, atol=1e-7, rtol=1e-6)
+    rp, ci, v = synth.banded_random_csr(1000, 3, 5, 64, "f64")
+    pat = ag.CsrPattern(rp.cuda(), ci.cuda(), 1000)
+    vals = v.cuda().requires_grad_()
+    xs = synth.uniform(1000, 4, "f64").cuda().requires_grad_()
+    assert torch.autograd.gradcheck(lambda vv, xx: ag.spmv(pat, vv, xx), (vals, xs), eps=1e-6,
+                                    atol=1e-7, rtol=1e-6)
+    a = synth.uniform(257, 5, "f64").cuda().requires_grad_()
+    b = synth.uniform(257, 6, "f64").cuda().requires_grad_()
+    assert torch.autograd.gradcheck(ag.dot, (a, b), eps=1e-6, atol=1e-7, rtol=1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_gemv_gradients_vs_oracle(storage):
+    ag = AG()
+    m, n = 300, 517
+    A = synth.normal((m, n), 7, storage).cuda().requires_grad_()
+    x = synth.uniform(n, 8, storage).cuda().requires_grad_()
+    dy = synth.uniform(m, 9, storage).cuda()
+    y = ag.gemv(A, x)
+    y.backward(dy)
+    torch.cuda.synchronize()
+    assert_normwise(host(y.detach()), oracle.gemv(A.detach().cpu(), x.detach().cpu(), m, n, n),
+                    storage)
+    ref_dA = oracle.round_to(oracle.dense_outer(dy.cpu(), x.detach().cpu()).ravel(), storage)
+    assert np.array_equal(host(A.grad), ref_dA)                # one rounded product each
+    ref_dx = oracle.gemv(A.detach().cpu(), dy.cpu(), n, m, n, "col")
+    assert_normwise(host(x.grad), ref_dx, storage)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_spmv_gradients_and_transpose_vs_oracle(storage):
+    ag = AG()
+    for rp, ci, v, n in ((*synth.laplacian_3d(24, storage), 24 ** 3),
+                         (*synth.powerlaw_csr(20_000, 15_000, 10, storage), 15_000),
+                         (*synth.random_csr(3000, 2000, 11, storage, 0, 30, 0.2, True), 2000)):
+        m = rp.numel() - 1
+        pat = ag.CsrPattern(rp.cuda(), ci.cuda(), n)
+        cp, ri, perm = pat.transpose()
+        ocp, ori, operm = oracle.csr_to_csc(rp, ci, n)
+        assert np.array_equal(cp.cpu().numpy(), ocp)
+        assert np.array_equal(ri.cpu().numpy(), ori)
+        assert np.array_equal(perm.cpu().numpy(), operm)
+        vals = v.cuda().requires_grad_()
+        x = synth.uniform(n, 12, storage).cuda().requires_grad_()
+        dy = synth.uniform(m, 13, storage).cuda()
+        y = ag.spmv(pat, vals, x)
+        y.backward(dy)
+        torch.cuda.synchronize()
+        ref_dv = oracle.round_to(oracle.sampled_outer(rp, ci, dy.cpu(), x.detach().cpu()), storage)
+        assert np.array_equal(host(vals.grad), ref_dv)
+        ref_dx = oracle.csr_spmv(ocp, ori, oracle.widen(v)[operm], dy.cpu())
+        assert_normwise(host(x.grad), ref_dx, storage)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_dot_gradients_vs_oracle(storage):
+    ag = AG()
+    n = 100_003
+    x = synth.uniform(n, 14, storage).cuda().requires_grad_()
+    y = synth.uniform(n, 15, storage).cuda().requires_grad_()
+    s = ag.dot(x, y)
+    ds = torch.tensor(1.75, dtype=s.dtype, device="cuda")
+    s.backward(ds)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(x.grad), oracle.round_to(oracle.scale(y.detach().cpu(), 1.75), storage))
+    assert np.array_equal(host(y.grad), oracle.round_to(oracle.scale(x.detach().cpu(), 1.75), storage))
+
+
+def test_differentiation_workload_sizes():
+    """The differentiation workload: dense 4096^2 FP32, CSR 3D Laplacian 64^3,
+    dot n = 1e7 -- forward and backward against the oracle."""
+    ag = AG()
+    m = n = 4096
+    g = torch.Generator(device="cuda").manual_seed(20)
+    A = torch.randn(m, n, generator=g, device="cuda").requires_grad_()
+    x = (torch.rand(n, generator=g, device="cuda") * 2 - 1).requires_grad_()
+    dy = torch.rand(m, generator=g, device="cuda") * 2 - 1
+    ag.gemv(A, x).backward(dy)
+    torch.cuda.synchronize()
+    rows = np.arange(0, m, 61)
+    ref = oracle.dense_outer(dy.cpu(), x.detach().cpu())
+    assert np.array_equal(host(A.grad).reshape(m, n)[rows], oracle.round_to(ref[rows].ravel(), "f32").reshape(len(rows), n))
+    assert_normwise(host(x.grad), oracle.gemv(A.detach().cpu(), dy.cpu(), n, m, n, "col"), "f32")
+    rp, ci, v = synth.laplacian_3d(64, "f32")
+    pat = ag.CsrPattern(rp.cuda(), ci.cuda(), 64 ** 3)
+    vals = v.cuda().requires_grad_()
+    xs = synth.uniform(64 ** 3, 21, "f32").cuda().requires_grad_()
+    dys = synth.uniform(64 ** 3, 22, "f32").cuda()
+    ag.spmv(pat, vals, xs).backward(dys)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(vals.grad), oracle.round_to(oracle.sampled_outer(rp, ci, dys.cpu(), xs.detach().cpu()), "f32"))
+    # the Laplacian is symmetric: A^T dy = A dy
+    assert_normwise(host(xs.grad), oracle.csr_spmv(rp, ci, v, dys.cpu()), "f32")
+    a = synth.uniform(10_000_000, 23, "f32").cuda().requires_grad_()
+    b = synth.uniform(10_000_000, 24, "f32").cuda().requires_grad_()
+    ag.dot(a, b).backward()
+    torch.cuda.synchronize()
+    assert torch.equal(a.grad, b.detach()) and torch.equal(b.grad, a.detach())
