@@ -575,6 +575,79 @@ def run_batched(device, reps=10, count=4096, seed=4000):
     return report
 
 
+def run_autograd(device, reps=20):
+    """Forward and backward of the differentiable products on the
+    differentiation workload: dense 4096^2 FP32 GEMV, CSR 3D Laplacian 64^3
+    FP32, dot n = 1e7 FP32.  Each backward kernel is timed on its own (L2
+    flushed by reading 256 MB before every launch) with its algorithmic bytes."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300 import autograd as ag
+
+    dev = device
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+
+    def rec(name, fn, nbytes):
+        for _ in range(3):
+            fn()
+        ms = _median_ms(fn, reps, flush)
+        out[name] = {"us": round(ms * 1e3, 2), "GBs": round(nbytes / (ms * 1e-3) / 1e9, 1)}
+
+    m = n = 4096
+    A = synth.device_normal_(torch.empty(m, n, device=dev), 1001)
+    x = synth.device_uniform_(torch.empty(n, device=dev), 1002)
+    dy = synth.device_uniform_(torch.empty(m, device=dev), 1003)
+    dA = torch.empty(m, n, device=dev)
+    dx = torch.empty(n, device=dev)
+    rec("gemv_forward", lambda: lak.dense_gemv(A, x), (m * n + m + n) * 4)
+    rec("gemv_backward_dA_outer", lambda: lak.dense_outer(dy, x, out=dA), (m * n + m + n) * 4)
+    rec("gemv_backward_dx_transposed", lambda: lak.dense_gemv(A.t(), dy, y=dx), (m * n + m + n) * 4)
+    Ar = A.clone().requires_grad_()
+    xr = x.clone().requires_grad_()
+
+    def full():
+        Ar.grad = None
+        xr.grad = None
+        ag.gemv(Ar, xr).backward(dy)
+    rec("gemv_forward_backward_autograd", full, 3 * (m * n + m + n) * 4)
+
+    rp, ci, v = synth.laplacian_3d(64, "f32")
+    mm = rp.numel() - 1
+    nnz = v.numel()
+    pat = ag.CsrPattern(rp.to(dev), ci.to(dev), mm)
+    vals = v.to(dev)
+    xs = synth.device_uniform_(torch.empty(mm, device=dev), 1004)
+    dys = synth.device_uniform_(torch.empty(mm, device=dev), 1005)
+    spmv_bytes = nnz * 8 + (mm + 1) * 4 + 2 * mm * 4
+    rec("spmv_forward", lambda: lak.csr_spmv(pat.row_ptr, pat.col_idx, vals, xs), spmv_bytes)
+    torch.cuda.synchronize()
+    import time
+    t0 = time.perf_counter()
+    cp, ri, perm = lak.csr_transpose(pat.row_ptr, pat.col_idx, mm)
+    torch.cuda.synchronize()
+    out["spmv_transpose_prepare_once_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    pat._t = (cp, ri, perm)
+    dv = torch.empty(nnz, device=dev)
+    vt = torch.empty(nnz, device=dev)
+    rec("spmv_backward_dvals_sampled", lambda: lak.csr_sampled_outer(pat.row_ptr, pat.col_idx, dys,
+                                                                   xs, out=dv),
+        nnz * 4 + nnz * 4 + (mm + 1) * 4 + 2 * mm * 4)
+    rec("spmv_backward_gather_values", lambda: lak.vec_gather(vals, perm, out=vt), nnz * 12)
+    rec("spmv_backward_dx_transposed", lambda: lak.csr_spmv(cp, ri, vt, dys), spmv_bytes)
+
+    nd = 10_000_000
+    a = synth.device_uniform_(torch.empty(nd, device=dev), 1006)
+    b = synth.device_uniform_(torch.empty(nd, device=dev), 1007)
+    ds = torch.ones(1, device=dev)
+    da = torch.empty_like(a)
+    rec("dot_forward", lambda: lak.vec_dot(a, b), nd * 8)
+    rec("dot_backward_scale", lambda: lak.vec_scale_dev(b, ds, out=da), nd * 8)
+    return out
+
+
 def recorded_traffic(path, name):
     """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
     when there is no record or the kernel's source changed since the capture."""
@@ -851,6 +924,9 @@ def run_gb300(args):
     batched = None
     if not args.no_batched and not args.only and rank == 0:
         batched = run_batched(device)
+    autograd = None
+    if not args.no_autograd and not args.only and rank == 0:
+        autograd = run_autograd(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -875,6 +951,8 @@ def run_gb300(args):
         line["precision"] = precision
     if batched is not None:
         line["batched"] = batched
+    if autograd is not None:
+        line["autograd"] = autograd
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -943,6 +1021,8 @@ def main(argv=None):
                     help="skip the BF16/FP16-storage and compensated-dot report")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (4096 uneven instances per family) report")
+    ap.add_argument("--no-autograd", action="store_true",
+                    help="skip the forward/backward (differentiation) report")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")
