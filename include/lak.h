@@ -153,6 +153,39 @@ LAK_API lak_status vec_axpy(void *x, const void *y, const void *z, double alpha,
                             void *stream);
 
 /*
+ * vec_axpby: x[i] = alpha * y[i] + beta * z[i]  (Sec. 2's scaled vector
+ * addition in its general form).  alpha and beta are rounded to the arithmetic
+ * type; each element is fl(alpha*y + fl(beta*z)) (one product rounded, then one
+ * fused multiply-add), rounded once more to the storage type for BF16/FP16.
+ * x may equal y or z.  Launch configuration as for vec_axpy.
+ */
+LAK_API lak_status vec_axpby(void *x, double alpha, const void *y, double beta, const void *z,
+                             int64_t n, lak_dtype dtype, const lak_cfg *cfg, void *stream);
+
+/*
+ * vec_axpby_strided: the same on strided vectors -- element i of x is
+ * x[i*incx] (likewise y, z); increments are in elements, may be negative (the
+ * pointer then addresses element 0, the highest address) and must not make x
+ * overlap itself (incx != 0).  Scalar accesses: the paper notes that its wide
+ * vector types suit strided access poorly (Sec. 2).
+ */
+LAK_API lak_status vec_axpby_strided(void *x, int64_t incx, double alpha, const void *y,
+                                     int64_t incy, double beta, const void *z, int64_t incz,
+                                     int64_t n, lak_dtype dtype, void *stream);
+
+/*
+ * vec_axpy_norm2: x[i] = y[i] + alpha * z[i] and *out = sum_i x[i]^2 of the
+ * stored x, in one pass (the update fused with the inner product of its result
+ * with itself: 3n elements moved instead of 5n for vec_axpy then vec_dot).
+ * Reduction, `out` type and workspace rules as for vec_dot; the workspace size
+ * comes from vec_axpy_norm2_workspace.
+ */
+LAK_API size_t vec_axpy_norm2_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg);
+LAK_API lak_status vec_axpy_norm2(void *x, const void *y, const void *z, double alpha, void *out,
+                                  int64_t n, lak_dtype dtype, void *workspace, size_t ws_bytes,
+                                  const lak_cfg *cfg, void *stream);
+
+/*
  * Workspace bytes vec_dot needs for these arguments on the current device
  * (a partial sum per block and one arrival counter).  0 on invalid input.
  */
@@ -241,6 +274,26 @@ LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m,
                               int64_t n, int64_t lda, lak_layout layout,
                               lak_dtype dtype, void *workspace, size_t ws_bytes,
                               const lak_cfg *cfg, void *stream);
+
+/*
+ * dense_gemv_axpby: y = alpha * A x + beta * y, same layouts, workspace and
+ * configuration as dense_gemv (the GEMV and the vector update fused: y is read
+ * only when beta != 0).  dense_gemv is the alpha = 1, beta = 0 case.
+ */
+LAK_API lak_status dense_gemv_axpby(void *y, double alpha, const void *A, const void *x,
+                                    double beta, int64_t m, int64_t n, int64_t lda,
+                                    lak_layout layout, lak_dtype dtype, void *workspace,
+                                    size_t ws_bytes, const lak_cfg *cfg, void *stream);
+
+/*
+ * dense_gemv_trans: y = A^T x for the m-by-n matrix A stored as for dense_gemv
+ * (y has n elements, x has m): the product in the other layout of the same
+ * storage.  Workspace: dense_gemv_workspace(n, m, <the other layout>, ...).
+ */
+LAK_API lak_status dense_gemv_trans(void *y, const void *A, const void *x, int64_t m, int64_t n,
+                                    int64_t lda, lak_layout layout, lak_dtype dtype,
+                                    void *workspace, size_t ws_bytes, const lak_cfg *cfg,
+                                    void *stream);
 
 /*
  * csr_spmv: y[i] = sum_{k=row_ptr[i]}^{row_ptr[i+1]-1} vals[k] * x[col_idx[k]]

@@ -23,7 +23,7 @@ import torch
 from . import _native
 from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
-__all__ = ["vec_copy", "vec_axpy", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
+__all__ = ["vec_copy", "vec_axpy", "vec_axpby", "vec_axpy_norm2", "dense_gemv_trans", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
            "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg", "Cfg",
@@ -155,6 +155,52 @@ def vec_axpy(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, alpha: float,
     return x
 
 
+def vec_axpby(x: torch.Tensor, alpha: float, y: torch.Tensor, beta: float, z: torch.Tensor,
+              cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """x[:] = alpha*y + beta*z; 1-D views with any (nonzero for x) strides take
+    the strided kernel, contiguous ones the vectorised kernel."""
+    s = _same_storage(x, y, z)
+    n = x.numel()
+    if y.numel() != n or z.numel() != n:
+        raise ValueError("x, y, z must have the same length")
+    if x.dim() != 1 or y.dim() != 1 or z.dim() != 1:
+        raise ValueError("x, y, z must be 1-D")
+    for t, nm in ((x, "x"), (y, "y"), (z, "z")):
+        _dev_ptr(t, nm)
+    if all(t.stride(0) == 1 or n <= 1 for t in (x, y, z)):
+        st = _lib.vec_axpby(x.data_ptr(), float(alpha), y.data_ptr(), float(beta), z.data_ptr(),
+                            n, DTYPES[s], _cfg_ptr(cfg), _stream(stream))
+        _native.check("vec_axpby", st)
+    else:
+        st = _lib.vec_axpby_strided(x.data_ptr(), x.stride(0), float(alpha), y.data_ptr(),
+                                    y.stride(0), float(beta), z.data_ptr(), z.stride(0), n,
+                                    DTYPES[s], _stream(stream))
+        _native.check("vec_axpby_strided", st)
+    return x
+
+
+def vec_axpy_norm2(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, alpha: float,
+                   out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                   cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """x[:] = y + alpha*z and returns <x, x> (one-element device tensor), in one pass."""
+    s = _same_storage(x, y, z)
+    n = x.numel()
+    if y.numel() != n or z.numel() != n:
+        raise ValueError("x, y, z must have the same length")
+    odt = torch.float64 if s == "f64" else torch.float32
+    if out is None:
+        out = torch.empty(1, dtype=odt, device=x.device)
+    sh = _stream(stream)
+    need = int(_lib.vec_axpy_norm2_workspace(n, DTYPES[s], _cfg_ptr(cfg)))
+    if workspace is None:
+        workspace = _workspace(need, sh, x.device)
+    st = _lib.vec_axpy_norm2(_vec_arg(x, "x"), _vec_arg(y, "y"), _vec_arg(z, "z"), float(alpha),
+                             _dev_ptr(out, "out"), n, DTYPES[s], _dev_ptr(workspace, "workspace"),
+                             workspace.numel(), _cfg_ptr(cfg), sh)
+    _native.check("vec_axpy_norm2", st)
+    return out
+
+
 def vec_dot_workspace(n: int, storage: str, cfg: CfgLike = None) -> int:
     return int(_lib.vec_dot_workspace(int(n), DTYPES[storage], _cfg_ptr(cfg)))
 
@@ -250,9 +296,11 @@ def _matrix_layout(A: torch.Tensor):
 def dense_gemv(A: torch.Tensor, x: torch.Tensor, y: Optional[torch.Tensor] = None,
                m: Optional[int] = None, n: Optional[int] = None, lda: Optional[int] = None,
                layout: Optional[str] = None, workspace: Optional[torch.Tensor] = None,
-               cfg: CfgLike = None, stream=None) -> torch.Tensor:
-    """y = A x.  A is a 2-D tensor (its strides give the layout and lda), or a
-    1-D buffer with explicit m, n, lda and layout ('row' or 'col')."""
+               cfg: CfgLike = None, stream=None, alpha: float = 1.0,
+               beta: float = 0.0) -> torch.Tensor:
+    """y = alpha * A x + beta * y (y is not read when beta == 0).  A is a 2-D
+    tensor (its strides give the layout and lda), or a 1-D buffer with
+    explicit m, n, lda and layout ('row' or 'col')."""
     s = _same_storage(A, x)
     if A.dim() == 2 and m is None:
         m, n, lda, lay = _matrix_layout(A)
@@ -278,9 +326,41 @@ def dense_gemv(A: torch.Tensor, x: torch.Tensor, y: Optional[torch.Tensor] = Non
             workspace = _workspace(need, sh, A.device)
         ws_ptr = _dev_ptr(workspace, "workspace")
         ws_bytes = workspace.numel() * workspace.element_size()
-    st = _lib.dense_gemv(_vec_arg(y, "y"), _dev_ptr(A, "A"), _vec_arg(x, "x"), int(m), int(n),
-                         int(lda), LAYOUTS[layout], DTYPES[s], ws_ptr, ws_bytes, _cfg_ptr(cfg), sh)
-    _native.check("dense_gemv", st)
+    if alpha == 1.0 and beta == 0.0:
+        st = _lib.dense_gemv(_vec_arg(y, "y"), _dev_ptr(A, "A"), _vec_arg(x, "x"), int(m), int(n),
+                             int(lda), LAYOUTS[layout], DTYPES[s], ws_ptr, ws_bytes, _cfg_ptr(cfg),
+                             sh)
+        _native.check("dense_gemv", st)
+    else:
+        st = _lib.dense_gemv_axpby(_vec_arg(y, "y"), float(alpha), _dev_ptr(A, "A"),
+                                   _vec_arg(x, "x"), float(beta), int(m), int(n), int(lda),
+                                   LAYOUTS[layout], DTYPES[s], ws_ptr, ws_bytes, _cfg_ptr(cfg), sh)
+        _native.check("dense_gemv_axpby", st)
+    return y
+
+
+def dense_gemv_trans(A: torch.Tensor, x: torch.Tensor, y: Optional[torch.Tensor] = None,
+                     workspace: Optional[torch.Tensor] = None, cfg: CfgLike = None,
+                     stream=None) -> torch.Tensor:
+    """y = A^T x for a 2-D tensor A (row- or column-major), through the
+    dense_gemv_trans entry point."""
+    s = _same_storage(A, x)
+    m, n, lda, layout = _matrix_layout(A)
+    if x.numel() != m:
+        raise ValueError(f"x has {x.numel()} elements, expected m={m}")
+    if y is None:
+        y = torch.empty(n, dtype=A.dtype, device=A.device)
+    other = "col" if layout == "row" else "row"
+    sh = _stream(stream)
+    need = dense_gemv_workspace(n, m, other, s, cfg)
+    ws_ptr, ws_bytes = None, 0
+    if need > 0:
+        if workspace is None:
+            workspace = _workspace(need, sh, A.device)
+        ws_ptr, ws_bytes = _dev_ptr(workspace, "workspace"), workspace.numel()
+    st = _lib.dense_gemv_trans(_vec_arg(y, "y"), _dev_ptr(A, "A"), _vec_arg(x, "x"), m, n, lda,
+                               LAYOUTS[layout], DTYPES[s], ws_ptr, ws_bytes, _cfg_ptr(cfg), sh)
+    _native.check("dense_gemv_trans", st)
     return y
 
 

@@ -23,9 +23,11 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 
 # exported symbols, in header order (checked by the ABI test)
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
-           "vec_copy", "vec_axpy", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
+           "vec_copy", "vec_axpy", "vec_axpby", "vec_axpby_strided", "vec_axpy_norm2_workspace",
+           "vec_axpy_norm2", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
            "vec_dot_noalloc",
-           "dense_gemv_workspace", "dense_gemv", "csr_spmv", "dense_outer", "csr_sampled_outer",
+           "dense_gemv_workspace", "dense_gemv", "dense_gemv_axpby", "dense_gemv_trans",
+           "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose_workspace", "csr_transpose", "vec_gather", "vec_scale_dev",
            "lak_batch_plan", "lak_batch_run")
 
@@ -89,12 +91,20 @@ _SIGNATURES = {
     "lak_resolve_cfg": (_I32, [_I32, _I32, _I64, _I64, _I64, _CFGP, _CFGP]),
     "vec_copy": (_I32, [_P, _P, _I64, _I32, _CFGP, _P]),
     "vec_axpy": (_I32, [_P, _P, _P, ctypes.c_double, _I64, _I32, _CFGP, _P]),
+    "vec_axpby": (_I32, [_P, ctypes.c_double, _P, ctypes.c_double, _P, _I64, _I32, _CFGP, _P]),
+    "vec_axpby_strided": (_I32, [_P, _I64, ctypes.c_double, _P, _I64, ctypes.c_double, _P, _I64,
+                                 _I64, _I32, _P]),
+    "vec_axpy_norm2_workspace": (_SZ, [_I64, _I32, _CFGP]),
+    "vec_axpy_norm2": (_I32, [_P, _P, _P, ctypes.c_double, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "vec_dot_workspace": (_SZ, [_I64, _I32, _CFGP]),
     "vec_dot": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "vec_dot_noalloc": (_I32, [_P, _P, _P, _I64, _I32, _CFGP, _P]),
     "vec_dot_compensated": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "dense_gemv_workspace": (_SZ, [_I64, _I64, _I32, _I32, _CFGP]),
     "dense_gemv": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
+    "dense_gemv_axpby": (_I32, [_P, ctypes.c_double, _P, _P, ctypes.c_double, _I64, _I64, _I64,
+                                _I32, _I32, _P, _SZ, _CFGP, _P]),
+    "dense_gemv_trans": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _I32, _P, _SZ, _CFGP, _P]),
     "csr_spmv": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
     "dense_outer": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I32, _P]),
     "csr_sampled_outer": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I32, _P]),

@@ -26,10 +26,20 @@
 namespace lak {
 namespace {
 
+// y = alpha * t + beta * y; y is not read when beta == 0 (it may hold anything)
+template <typename T>
+__device__ __forceinline__ T gemv_epilogue(typename Acc<T>::type t, typename Acc<T>::type alpha,
+                                           typename Acc<T>::type beta, const T *yold) {
+    using Ac = typename Acc<T>::type;
+    if (beta == Ac(0)) return narrow<T>(alpha * t);
+    return narrow<T>(fma_acc(alpha, t, beta * widen(*yold)));
+}
+
 template <typename T, int V>
 __global__ void __launch_bounds__(512)
 gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict__ x, int64_t m,
-                int64_t n, int64_t lda, int G, int inc) {
+                int64_t n, int64_t lda, int G, int inc, typename Acc<T>::type alpha,
+                typename Acc<T>::type beta) {
     using Ac = typename Acc<T>::type;
     __shared__ Ac red[32];
     const int R = blockDim.x / G;                  // rows per block step
@@ -62,7 +72,7 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         Ac s = acc[0];
         if (G <= 32) {
             s = group_sum(s, G);
-            if (lg == 0 && row < row_end) y[row] = narrow<T>(s);
+            if (lg == 0 && row < row_end) y[row] = gemv_epilogue<T>(s, alpha, beta, y + row);
         } else {
             s = group_sum(s, 32);
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -71,7 +81,7 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
                 const int wpg = G >> 5;
                 Ac t = Ac(0);
                 for (int w = 0; w < wpg; ++w) t += red[grp * wpg + w];
-                y[row] = narrow<T>(t);
+                y[row] = gemv_epilogue<T>(t, alpha, beta, y + row);
             }
             __syncthreads();
         }
@@ -82,7 +92,8 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 gemv_col_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict__ x, int64_t m,
                 int64_t n, int64_t lda, int64_t cols_per_split,
-                typename Acc<T>::type *__restrict__ partials, unsigned int *__restrict__ tickets) {
+                typename Acc<T>::type *__restrict__ partials, unsigned int *__restrict__ tickets,
+                typename Acc<T>::type alpha, typename Acc<T>::type beta) {
     using Ac = typename Acc<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ac *red = reinterpret_cast<Ac *>(smem_raw);    // [nwarps][32*V]
@@ -129,7 +140,7 @@ gemv_col_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         const int64_t row = tile0 + rr;
         if (row < m) {
             if (nsplit == 1)
-                y[row] = narrow<T>(t);
+                y[row] = gemv_epilogue<T>(t, alpha, beta, y + row);
             else
                 partials[(int64_t)split * m + row] = t;
         }
@@ -150,19 +161,21 @@ gemv_col_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         if (row < m) {
             Ac t = Ac(0);
             for (int s2 = 0; s2 < nsplit; ++s2) t += __ldcg(partials + (int64_t)s2 * m + row);
-            y[row] = narrow<T>(t);
+            y[row] = gemv_epilogue<T>(t, alpha, beta, y + row);
         }
     }
 }
 
 template <typename T>
 lak_status gemv_row_t(void *y, const void *A, const void *x, int64_t m, int64_t n, int64_t lda,
-                      const Launch &L, int G, cudaStream_t s) {
+                      const Launch &L, int G, double alpha, double beta, cudaStream_t s) {
+    using Ac = typename Acc<T>::type;
     T *yp = static_cast<T *>(y);
     const T *Ap = static_cast<const T *>(A);
     const T *xp = static_cast<const T *>(x);
 #define LAK_ROW(VV) \
-    gemv_row_kernel<T, VV><<<L.grid, L.block, 0, s>>>(yp, Ap, xp, m, n, lda, G, L.inc)
+    gemv_row_kernel<T, VV><<<L.grid, L.block, 0, s>>>(yp, Ap, xp, m, n, lda, G, L.inc, (Ac)alpha, \
+                                                      (Ac)beta)
     switch (L.vec) {
     case 1: LAK_ROW(1); break;
     case 2: LAK_ROW(2); break;
@@ -177,7 +190,8 @@ lak_status gemv_row_t(void *y, const void *A, const void *x, int64_t m, int64_t 
 
 template <typename T>
 lak_status gemv_col_t(void *y, const void *A, const void *x, int64_t m, int64_t n, int64_t lda,
-                      const Launch &L, int splits, void *ws, cudaStream_t s) {
+                      const Launch &L, int splits, void *ws, double alpha, double beta,
+                      cudaStream_t s) {
     using Ac = typename Acc<T>::type;
     T *yp = static_cast<T *>(y);
     const T *Ap = static_cast<const T *>(A);
@@ -200,7 +214,8 @@ lak_status gemv_col_t(void *y, const void *A, const void *x, int64_t m, int64_t 
                             cudaGetErrorString(e));                                           \
         }                                                                                     \
         gemv_col_kernel<T, VV><<<grid, L.block, smem, s>>>(yp, Ap, xp, m, n, lda, cps,        \
-                                                           partials, tickets);                \
+                                                           partials, tickets, (Ac)alpha,      \
+                                                           (Ac)beta);                         \
     } while (0)
     switch (L.vec) {
     case 1: LAK_COL(1); break;
@@ -217,24 +232,26 @@ lak_status gemv_col_t(void *y, const void *A, const void *x, int64_t m, int64_t 
 }  // namespace
 
 lak_status launch_gemv_row(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
-                           int64_t n, int64_t lda, const Launch &L, int group, cudaStream_t s) {
+                           int64_t n, int64_t lda, const Launch &L, int group, double alpha,
+                           double beta, cudaStream_t s) {
     switch (dt) {
-    case LAK_F32: return gemv_row_t<float>(y, A, x, m, n, lda, L, group, s);
-    case LAK_F64: return gemv_row_t<double>(y, A, x, m, n, lda, L, group, s);
-    case LAK_BF16: return gemv_row_t<__nv_bfloat16>(y, A, x, m, n, lda, L, group, s);
-    case LAK_F16: return gemv_row_t<__half>(y, A, x, m, n, lda, L, group, s);
+    case LAK_F32: return gemv_row_t<float>(y, A, x, m, n, lda, L, group, alpha, beta, s);
+    case LAK_F64: return gemv_row_t<double>(y, A, x, m, n, lda, L, group, alpha, beta, s);
+    case LAK_BF16: return gemv_row_t<__nv_bfloat16>(y, A, x, m, n, lda, L, group, alpha, beta, s);
+    case LAK_F16: return gemv_row_t<__half>(y, A, x, m, n, lda, L, group, alpha, beta, s);
     }
     return fail(LAK_EDTYPE, "dense_gemv: unknown dtype %d", (int)dt);
 }
 
 lak_status launch_gemv_col(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
                            int64_t n, int64_t lda, const Launch &L, int splits, void *ws,
-                           cudaStream_t s) {
+                           double alpha, double beta, cudaStream_t s) {
     switch (dt) {
-    case LAK_F32: return gemv_col_t<float>(y, A, x, m, n, lda, L, splits, ws, s);
-    case LAK_F64: return gemv_col_t<double>(y, A, x, m, n, lda, L, splits, ws, s);
-    case LAK_BF16: return gemv_col_t<__nv_bfloat16>(y, A, x, m, n, lda, L, splits, ws, s);
-    case LAK_F16: return gemv_col_t<__half>(y, A, x, m, n, lda, L, splits, ws, s);
+    case LAK_F32: return gemv_col_t<float>(y, A, x, m, n, lda, L, splits, ws, alpha, beta, s);
+    case LAK_F64: return gemv_col_t<double>(y, A, x, m, n, lda, L, splits, ws, alpha, beta, s);
+    case LAK_BF16:
+        return gemv_col_t<__nv_bfloat16>(y, A, x, m, n, lda, L, splits, ws, alpha, beta, s);
+    case LAK_F16: return gemv_col_t<__half>(y, A, x, m, n, lda, L, splits, ws, alpha, beta, s);
     }
     return fail(LAK_EDTYPE, "dense_gemv: unknown dtype %d", (int)dt);
 }

@@ -563,40 +563,159 @@ LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout, lak
     return best;
 }
 
-LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m, int64_t n,
-                              int64_t lda, lak_layout layout, lak_dtype dtype, void *workspace,
-                              size_t ws_bytes, const lak_cfg *cfg, void *stream) {
-    lak_status st = common_checks("dense_gemv", dtype, cfg);
+}  // extern "C"
+
+namespace {
+
+lak_status gemv_impl(const char *who, void *y, const void *A, const void *x, int64_t m, int64_t n,
+                     int64_t lda, lak_layout layout, lak_dtype dtype, void *workspace,
+                     size_t ws_bytes, const lak_cfg *cfg, double alpha, double beta,
+                     void *stream) {
+    lak_status st = common_checks(who, dtype, cfg);
     if (st != LAK_OK) return st;
     if (layout != LAK_ROW_MAJOR && layout != LAK_COL_MAJOR)
-        return fail(LAK_ELAYOUT, "dense_gemv: unknown layout %d", (int)layout);
-    if (m < 0 || n < 0) return fail(LAK_EINVAL, "dense_gemv: negative size");
+        return fail(LAK_ELAYOUT, "%s: unknown layout %d", who, (int)layout);
+    if (m < 0 || n < 0) return fail(LAK_EINVAL, "%s: negative size", who);
     const int64_t ld_min = layout == LAK_ROW_MAJOR ? (n > 1 ? n : 1) : (m > 1 ? m : 1);
     if (lda < ld_min)
-        return fail(LAK_EINVAL, "dense_gemv: lda=%lld < %lld", (long long)lda, (long long)ld_min);
+        return fail(LAK_EINVAL, "%s: lda=%lld < %lld", who, (long long)lda, (long long)ld_min);
     if (m == 0) return LAK_OK;
     const int es = esize(dtype);
-    if (!y || (n > 0 && (!A || !x))) return fail(LAK_EINVAL, "dense_gemv: NULL pointer");
+    if (!y || (n > 0 && (!A || !x))) return fail(LAK_EINVAL, "%s: NULL pointer", who);
     if (!aligned_elem(y, es) || !aligned_elem(A, es) || !aligned_elem(x, es))
-        return fail(LAK_EINVAL, "dense_gemv: pointers not aligned to the element size");
+        return fail(LAK_EINVAL, "%s: pointers not aligned to the element size", who);
     cudaStream_t s = (cudaStream_t)stream;
     if (layout == LAK_ROW_MAJOR) {
         RowPlan p;
         st = plan_gemv_row(dtype, m, n, lda, cfg, A, x, &p);
         if (st != LAK_OK) return st;
-        return launch_gemv_row(dtype, y, A, x, m, n, lda, p.L, p.group, s);
+        return launch_gemv_row(dtype, y, A, x, m, n, lda, p.L, p.group, alpha, beta, s);
     }
     ColPlan p;
     st = plan_gemv_col(dtype, m, n, lda, cfg, A, &p);
     if (st != LAK_OK) return st;
     if (p.ws_bytes > 0) {
         if (!workspace || ws_bytes < p.ws_bytes)
-            return fail(LAK_EWORKSPACE, "dense_gemv: workspace of %zu bytes needed, %zu given",
+            return fail(LAK_EWORKSPACE, "%s: workspace of %zu bytes needed, %zu given", who,
                         p.ws_bytes, workspace ? ws_bytes : (size_t)0);
         if ((uintptr_t)workspace % 256)
-            return fail(LAK_EWORKSPACE, "dense_gemv: workspace not 256-byte aligned");
+            return fail(LAK_EWORKSPACE, "%s: workspace not 256-byte aligned", who);
     }
-    return launch_gemv_col(dtype, y, A, x, m, n, lda, p.L, p.splits, workspace, s);
+    return launch_gemv_col(dtype, y, A, x, m, n, lda, p.L, p.splits, workspace, alpha, beta, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m, int64_t n,
+                              int64_t lda, lak_layout layout, lak_dtype dtype, void *workspace,
+                              size_t ws_bytes, const lak_cfg *cfg, void *stream) {
+    return gemv_impl("dense_gemv", y, A, x, m, n, lda, layout, dtype, workspace, ws_bytes, cfg,
+                     1.0, 0.0, stream);
+}
+
+LAK_API lak_status dense_gemv_axpby(void *y, double alpha, const void *A, const void *x,
+                                    double beta, int64_t m, int64_t n, int64_t lda,
+                                    lak_layout layout, lak_dtype dtype, void *workspace,
+                                    size_t ws_bytes, const lak_cfg *cfg, void *stream) {
+    return gemv_impl("dense_gemv_axpby", y, A, x, m, n, lda, layout, dtype, workspace, ws_bytes,
+                     cfg, alpha, beta, stream);
+}
+
+LAK_API lak_status dense_gemv_trans(void *y, const void *A, const void *x, int64_t m, int64_t n,
+                                    int64_t lda, lak_layout layout, lak_dtype dtype,
+                                    void *workspace, size_t ws_bytes, const lak_cfg *cfg,
+                                    void *stream) {
+    if (layout != LAK_ROW_MAJOR && layout != LAK_COL_MAJOR)
+        return fail(LAK_ELAYOUT, "dense_gemv_trans: unknown layout %d", (int)layout);
+    // A^T of an m-by-n matrix in one layout is an n-by-m matrix in the other
+    const lak_layout other = layout == LAK_ROW_MAJOR ? LAK_COL_MAJOR : LAK_ROW_MAJOR;
+    return gemv_impl("dense_gemv_trans", y, A, x, n, m, lda, other, dtype, workspace, ws_bytes,
+                     cfg, 1.0, 0.0, stream);
+}
+
+LAK_API size_t vec_axpy_norm2_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg) {
+    if (!valid_dtype(dtype) || n < 0 || check_cfg(cfg, "vec_axpy_norm2_workspace") != LAK_OK)
+        return 0;
+    VecPlan p, p1;
+    if (plan_vector(LAK_OP_AXPY, dtype, n, cfg, nullptr, 0, &p) != LAK_OK) return 0;
+    lak_cfg c = base_cfg(LAK_OP_AXPY, dtype, cfg);
+    c.vec = 1;
+    if (plan_vector(LAK_OP_AXPY, dtype, n, &c, nullptr, 0, &p1) != LAK_OK) return 0;
+    const int grid = p1.L.grid > p.L.grid ? p1.L.grid : p.L.grid;
+    return (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)grid;
+}
+
+LAK_API lak_status vec_axpy_norm2(void *x, const void *y, const void *z, double alpha, void *out,
+                                  int64_t n, lak_dtype dtype, void *workspace, size_t ws_bytes,
+                                  const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_axpy_norm2", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (n < 0) return fail(LAK_EINVAL, "vec_axpy_norm2: n=%lld < 0", (long long)n);
+    if (!out) return fail(LAK_EINVAL, "vec_axpy_norm2: NULL out");
+    const int out_bytes = dtype == LAK_F64 ? 8 : 4;
+    if ((uintptr_t)out % out_bytes) return fail(LAK_EINVAL, "vec_axpy_norm2: out misaligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        const cudaError_t e = cudaMemsetAsync(out, 0, out_bytes, s);
+        if (e != cudaSuccess)
+            return fail(LAK_ECUDA, "vec_axpy_norm2: memset: %s", cudaGetErrorString(e));
+        return LAK_OK;
+    }
+    const int es = esize(dtype);
+    if (!x || !y || !z) return fail(LAK_EINVAL, "vec_axpy_norm2: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es) || !aligned_elem(z, es))
+        return fail(LAK_EINVAL, "vec_axpy_norm2: pointers not aligned to the element size");
+    const void *ptrs[3] = {x, y, z};
+    VecPlan p;
+    st = plan_vector(LAK_OP_AXPY, dtype, n, cfg, ptrs, 3, &p);
+    if (st != LAK_OK) return st;
+    const size_t need = (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)p.L.grid;
+    if (!workspace || ws_bytes < need)
+        return fail(LAK_EWORKSPACE, "vec_axpy_norm2: workspace of %zu bytes needed, %zu given",
+                    need, workspace ? ws_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256)
+        return fail(LAK_EWORKSPACE, "vec_axpy_norm2: workspace not 256-byte aligned");
+    return launch_axpy_norm2(dtype, x, y, z, alpha, out, n, workspace, p.L, p.head, s);
+}
+
+LAK_API lak_status vec_axpby(void *x, double alpha, const void *y, double beta, const void *z,
+                             int64_t n, lak_dtype dtype, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_axpby", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (n < 0) return fail(LAK_EINVAL, "vec_axpby: n=%lld < 0", (long long)n);
+    if (n == 0) return LAK_OK;
+    const int es = esize(dtype);
+    if (!x || !y || !z) return fail(LAK_EINVAL, "vec_axpby: NULL pointer");
+    if (!aligned_elem(x, es) || !aligned_elem(y, es) || !aligned_elem(z, es))
+        return fail(LAK_EINVAL, "vec_axpby: pointers not aligned to the element size");
+    const void *ptrs[3] = {x, y, z};
+    VecPlan p;
+    st = plan_vector(LAK_OP_AXPY, dtype, n, cfg, ptrs, 3, &p);
+    if (st != LAK_OK) return st;
+    return launch_axpby(dtype, x, alpha, y, beta, z, n, p.L, p.head, (cudaStream_t)stream);
+}
+
+LAK_API lak_status vec_axpby_strided(void *x, int64_t incx, double alpha, const void *y,
+                                     int64_t incy, double beta, const void *z, int64_t incz,
+                                     int64_t n, lak_dtype dtype, void *stream) {
+    if (!valid_dtype(dtype)) return fail(LAK_EDTYPE, "vec_axpby_strided: unknown dtype %d", (int)dtype);
+    if (n < 0) return fail(LAK_EINVAL, "vec_axpby_strided: n=%lld < 0", (long long)n);
+    if (n == 0) return LAK_OK;
+    if (!x || !y || !z) return fail(LAK_EINVAL, "vec_axpby_strided: NULL pointer");
+    if (incx == 0) return fail(LAK_EINVAL, "vec_axpby_strided: incx must not be 0");
+    const int es = esize(dtype);
+    if (!aligned_elem(x, es) || !aligned_elem(y, es) || !aligned_elem(z, es))
+        return fail(LAK_EINVAL, "vec_axpby_strided: pointers not aligned to the element size");
+    const DeviceInfo *di = device_info();
+    if (!di) return LAK_ECUDA;
+    const int block = 256;
+    int64_t grid = ceil_div(n, block);
+    const int64_t cap = (int64_t)di->sms * (di->max_threads_per_sm / block);
+    if (grid > cap) grid = cap;
+    return launch_axpby_strided(dtype, x, incx, alpha, y, incy, beta, z, incz, n, (int)grid, block,
+                                (cudaStream_t)stream);
 }
 
 LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_idx,

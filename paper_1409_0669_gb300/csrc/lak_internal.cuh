@@ -80,11 +80,21 @@ lak_status launch_dot(lak_dtype dt, void *out, const void *x, const void *y, int
                       void *ws, const Launch &L, int64_t head, cudaStream_t s);
 lak_status launch_dot_comp(lak_dtype dt, void *out, const void *x, const void *y, int64_t n,
                            void *ws, const Launch &L, int64_t head, cudaStream_t s);
+lak_status launch_axpby(lak_dtype dt, void *x, double alpha, const void *y, double beta,
+                        const void *z, int64_t n, const Launch &L, int64_t head, cudaStream_t s);
+lak_status launch_axpby_strided(lak_dtype dt, void *x, int64_t incx, double alpha, const void *y,
+                                int64_t incy, double beta, const void *z, int64_t incz, int64_t n,
+                                int grid, int block, cudaStream_t s);
+lak_status launch_axpy_norm2(lak_dtype dt, void *x, const void *y, const void *z, double alpha,
+                             void *out, int64_t n, void *ws, const Launch &L, int64_t head,
+                             cudaStream_t s);
+// GEMV launchers compute y = alpha*A*x + beta*y (y is not read when beta == 0).
 lak_status launch_gemv_row(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
-                           int64_t n, int64_t lda, const Launch &L, int group, cudaStream_t s);
+                           int64_t n, int64_t lda, const Launch &L, int group, double alpha,
+                           double beta, cudaStream_t s);
 lak_status launch_gemv_col(lak_dtype dt, void *y, const void *A, const void *x, int64_t m,
                            int64_t n, int64_t lda, const Launch &L, int splits, void *ws,
-                           cudaStream_t s);
+                           double alpha, double beta, cudaStream_t s);
 lak_status launch_spmv(lak_dtype dt, void *y, const int32_t *rp, const int32_t *ci,
                        const void *vals, const void *x, int64_t m, const Launch &L, int group,
                        cudaStream_t s);
