@@ -648,6 +648,64 @@ def run_autograd(device, reps=20):
     return out
 
 
+def run_fused(device, reps=20):
+    """Fused forms against their unfused sequences (FP32 and FP64, n = 1e8 /
+    16384^2): x = y + a z with <x, x> in one pass vs vec_axpy then vec_dot
+    (3n vs 5n elements moved), and y = a A x + b y vs dense_gemv plus a
+    separate update; L2 flushed (256 MB read) before every timed launch."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+
+    dev = device
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+    for storage in ("f32", "f64"):
+        dt = synth.torch_dtype(storage)
+        es = 8 if storage == "f64" else 4
+        n = 100_000_000
+        y = synth.device_uniform_(torch.empty(n, dtype=dt, device=dev), 1101)
+        z = synth.device_uniform_(torch.empty(n, dtype=dt, device=dev), 1102)
+        x = torch.empty_like(y)
+        ws = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+
+        def fused():
+            lak.vec_axpy_norm2(x, y, z, 0.5, workspace=ws)
+
+        def separate():
+            lak.vec_axpy(x, y, z, 0.5)
+            lak.vec_dot(x, x, workspace=ws)
+        for f in (fused, separate):
+            f()
+        tf = _median_ms(fused, reps, flush)
+        ts = _median_ms(separate, reps, flush)
+        out[f"axpy_norm2_{storage}"] = {"us_fused": round(tf * 1e3, 1),
+                                        "GBs_fused": round(3 * n * es / (tf * 1e-3) / 1e9, 1),
+                                        "us_separate": round(ts * 1e3, 1),
+                                        "speedup": round(ts / tf, 3)}
+        g = 16384
+        A = synth.device_normal_(torch.empty(g, g, dtype=dt, device=dev), 1103)
+        xg = synth.device_uniform_(torch.empty(g, dtype=dt, device=dev), 1104)
+        yg = synth.device_uniform_(torch.empty(g, dtype=dt, device=dev), 1105)
+        tmp = torch.empty_like(yg)
+
+        def gfused():
+            lak.dense_gemv(A, xg, y=yg, alpha=0.5, beta=-1.0)
+
+        def gseparate():
+            lak.dense_gemv(A, xg, y=tmp)
+            lak.vec_axpby(yg, -1.0, yg, 0.5, tmp)
+        for f in (gfused, gseparate):
+            f()
+        tf = _median_ms(gfused, reps, flush)
+        ts = _median_ms(gseparate, reps, flush)
+        out[f"gemv_axpby_{storage}"] = {"us_fused": round(tf * 1e3, 1), "us_separate": round(ts * 1e3, 1),
+                                        "speedup": round(ts / tf, 3)}
+        del y, z, x, A
+    return out
+
+
 def recorded_traffic(path, name):
     """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
     when there is no record or the kernel's source changed since the capture."""
@@ -927,6 +985,9 @@ def run_gb300(args):
     autograd = None
     if not args.no_autograd and not args.only and rank == 0:
         autograd = run_autograd(device)
+    fused = None
+    if not args.no_fused and not args.only and rank == 0:
+        fused = run_fused(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -953,6 +1014,8 @@ def run_gb300(args):
         line["batched"] = batched
     if autograd is not None:
         line["autograd"] = autograd
+    if fused is not None:
+        line["fused"] = fused
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -1023,6 +1086,8 @@ def main(argv=None):
                     help="skip the batched (4096 uneven instances per family) report")
     ap.add_argument("--no-autograd", action="store_true",
                     help="skip the forward/backward (differentiation) report")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="skip the fused-vs-separate report")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")

@@ -83,6 +83,9 @@ def _bind(path: str):
         "orc_round_f16": (None, [_U16P, _F64P, _I64]),
         "orc_widen_f16": (None, [_F64P, _U16P, _I64]),
         "orc_round_f32": (None, [_F32P, _F64P, _I64]),
+        "orc_csr_to_sell": (_I64, [_I32P, _I32P, _I64, _I64, _I64, _I32P, _I32P, _I64P, _I32P,
+                                   _I32P]),
+        "orc_sell_spmv": (None, [_F64P, _I64, _I64, _I32P, _I32P, _I64P, _I32P, _F64P, _F64P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -240,6 +243,38 @@ def csr_to_csc(row_ptr, col_idx, n: int):
     if rc != 0:
         raise MemoryError("oracle csr_to_csc: allocation failed")
     return col_ptr, row_idx[:nnz], perm[:nnz]
+
+
+def csr_to_sell(row_ptr, col_idx, C: int = 32, sigma: int = 1):
+    """SELL-C-sigma form: (perm, slice_len, slice_ptr, cols, map) -- see
+    lak_oracle.c for the layout."""
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    m = rp.size - 1
+    mp = (m + C - 1) // C * C
+    ns = mp // C
+    perm = np.empty(max(mp, 1), np.int32)
+    slen = np.empty(max(ns, 1), np.int32)
+    sptr = np.empty(ns + 1, np.int64)
+    lib = _load()
+    nil = ctypes.POINTER(ctypes.c_int32)()
+    total = lib.orc_csr_to_sell(_ptr(rp, _I32P), _ptr(ci, _I32P), m, C, sigma, _ptr(perm, _I32P),
+                                _ptr(slen, _I32P), _ptr(sptr, _I64P), nil, nil)
+    cols = np.empty(max(total, 1), np.int32)
+    mp_ = np.empty(max(total, 1), np.int32)
+    lib.orc_csr_to_sell(_ptr(rp, _I32P), _ptr(ci, _I32P), m, C, sigma, _ptr(perm, _I32P),
+                        _ptr(slen, _I32P), _ptr(sptr, _I64P), _ptr(cols, _I32P), _ptr(mp_, _I32P))
+    return perm[:mp], slen[:ns], sptr, cols[:total], mp_[:total]
+
+
+def sell_spmv(perm, slice_len, slice_ptr, cols, sell_vals, x, m: int, C: int = 32) -> np.ndarray:
+    """y = A x from SELL-C-sigma arrays (sell_vals in SELL slots)."""
+    pm, sl, co = _i32(perm), _i32(slice_len), _i32(cols)
+    sp = np.ascontiguousarray(np.asarray(slice_ptr), dtype=np.int64)
+    vv, xv = widen(sell_vals), widen(x)
+    y = np.zeros(m, np.float64)
+    _load().orc_sell_spmv(_ptr(y, _F64P), m, C, _ptr(pm, _I32P), _ptr(sl, _I32P), _ptr(sp, _I64P),
+                          _ptr(co, _I32P), _ptr(vv, _F64P), _ptr(xv, _F64P))
+    return y
 
 
 def dense_outer(dy, x) -> np.ndarray:

@@ -211,6 +211,101 @@ int orc_csr_to_csc(int32_t *col_ptr, int32_t *row_idx, int64_t *perm,
     return 0;
 }
 
+/* ---- sliced ELLPACK (SELL-C-sigma) ----------------------------------------- */
+
+/*
+ * SELL-C-sigma layout of an m-row CSR pattern with slices of C rows: within
+ * every window of `sigma` consecutive rows (sigma a multiple of C, or 1 for no
+ * sorting) rows are ordered by decreasing length, ties by increasing row index;
+ * position p of that order holds original row perm[p] (-1 past the last row,
+ * positions padded to a multiple of C).  Slice s (positions s*C .. s*C+C-1) is
+ * padded to its longest row: slice_len[s]; its entries start at slice_ptr[s]
+ * and entry j of the row at position s*C + r sits at slice_ptr[s] + j*C + r
+ * (column-major inside the slice).  cols holds the column, or -1 for padding;
+ * map holds the CSR position of the entry, or -1.  Returns the padded size
+ * when cols is NULL (first call), else fills the arrays and returns it.
+ */
+int64_t orc_csr_to_sell(const int32_t *row_ptr, const int32_t *col_idx, int64_t m, int64_t C,
+                        int64_t sigma, int32_t *perm, int32_t *slice_len, int64_t *slice_ptr,
+                        int32_t *cols, int32_t *map)
+{
+    int64_t mp = (m + C - 1) / C * C;
+    int64_t nslices = mp / C;
+    int64_t win = sigma > 1 ? sigma : 1;
+    /* order within windows: insertion sort of (length desc, index asc) */
+    for (int64_t w0 = 0; w0 < mp; w0 += win) {
+        int64_t w1 = w0 + win < mp ? w0 + win : mp;
+        for (int64_t p = w0; p < w1; ++p) perm[p] = p < m ? (int32_t)p : -1;
+        if (win > 1) {
+            for (int64_t p = w0 + 1; p < w1; ++p) {
+                int32_t r = perm[p];
+                int64_t lr = r >= 0 ? row_ptr[r + 1] - row_ptr[r] : -1;
+                int64_t q = p - 1;
+                while (q >= w0) {
+                    int32_t o = perm[q];
+                    int64_t lo = o >= 0 ? row_ptr[o + 1] - row_ptr[o] : -1;
+                    if (lo > lr || (lo == lr && (o >= 0 ? o : m + q) < (r >= 0 ? r : m + p))) break;
+                    perm[q + 1] = perm[q];
+                    --q;
+                }
+                perm[q + 1] = r;
+            }
+        }
+    }
+    int64_t total = 0;
+    for (int64_t s = 0; s < nslices; ++s) {
+        int64_t L = 0;
+        for (int64_t r = 0; r < C; ++r) {
+            int32_t i = perm[s * C + r];
+            int64_t l = i >= 0 ? row_ptr[i + 1] - row_ptr[i] : 0;
+            if (l > L) L = l;
+        }
+        slice_len[s] = (int32_t)L;
+        slice_ptr[s] = total;
+        total += L * C;
+    }
+    slice_ptr[nslices] = total;
+    if (!cols) return total;
+    for (int64_t s = 0; s < nslices; ++s) {
+        for (int64_t r = 0; r < C; ++r) {
+            int32_t i = perm[s * C + r];
+            int64_t l = i >= 0 ? row_ptr[i + 1] - row_ptr[i] : 0;
+            for (int64_t j = 0; j < slice_len[s]; ++j) {
+                int64_t slot = slice_ptr[s] + j * C + r;
+                if (j < l) {
+                    cols[slot] = col_idx[row_ptr[i] + j];
+                    map[slot] = (int32_t)(row_ptr[i] + j);
+                } else {
+                    cols[slot] = -1;
+                    map[slot] = -1;
+                }
+            }
+        }
+    }
+    return total;
+}
+
+/* y = A x from the SELL-C-sigma arrays above (vals in SELL slots; padding
+ * skipped); each row a compensated sum over its entries in stored order. */
+void orc_sell_spmv(double *y, int64_t m, int64_t C, const int32_t *perm,
+                   const int32_t *slice_len, const int64_t *slice_ptr, const int32_t *cols,
+                   const double *vals, const double *x)
+{
+    int64_t nslices = (m + C - 1) / C;
+    for (int64_t s = 0; s < nslices; ++s) {
+        for (int64_t r = 0; r < C; ++r) {
+            int32_t i = perm[s * C + r];
+            if (i < 0) continue;
+            orc_acc acc = {0.0, 0.0};
+            for (int64_t j = 0; j < slice_len[s]; ++j) {
+                int64_t slot = slice_ptr[s] + j * C + r;
+                if (cols[slot] >= 0) acc_add_prod(&acc, vals[slot], x[cols[slot]]);
+            }
+            y[i] = acc_value(&acc, NULL);
+        }
+    }
+}
+
 /* ---- gradients of the products (reverse mode) ---------------------------- */
 
 /* Dense y = A x:  dA = dy x^T, an m-by-n row-major outer product. */

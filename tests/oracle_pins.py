@@ -339,6 +339,62 @@ def pin_csc_transpose():
         assert np.array_equal(C.data, v[perm])
 
 
+# ---- SELL-C-sigma --------------------------------------------------------------------
+
+def pin_sell_layout_bruteforce():
+    m, n = 203, 150
+    rp, ci, v = synth.random_csr(m, n, 40, "f64", 0, 12, 0.15, True)
+    rp, ci = rp.numpy(), ci.numpy()
+    lens = np.diff(rp)
+    for sigma in (1, 32, 64, 256):
+        perm, slen, sptr, cols, mp = oracle.csr_to_sell(rp, ci, 32, sigma)
+        mpad = (m + 31) // 32 * 32
+        assert perm.size == mpad
+        assert sorted(int(p) for p in perm if p >= 0) == list(range(m))
+        assert np.all(perm[m:] == -1) if sigma == 1 else np.sum(perm < 0) == mpad - m
+        win = max(sigma, 1)
+        for w0 in range(0, mpad, win):
+            blk = perm[w0:w0 + win]
+            assert set(int(p) for p in blk if p >= 0) == set(range(w0, min(w0 + win, m)))
+            if sigma > 1:
+                key = [(-lens[p], p) if p >= 0 else (1, 10 ** 9 + q) for q, p in enumerate(blk)]
+                assert key == sorted(key)
+        total = 0
+        for s_ in range(mpad // 32):
+            L = max([lens[p] if p >= 0 else 0 for p in perm[32 * s_:32 * s_ + 32]])
+            assert slen[s_] == L and sptr[s_] == total
+            total += 32 * L
+            for r in range(32):
+                i = perm[32 * s_ + r]
+                li = lens[i] if i >= 0 else 0
+                for j in range(L):
+                    slot = sptr[s_] + 32 * j + r
+                    if j < li:
+                        assert cols[slot] == ci[rp[i] + j] and mp[slot] == rp[i] + j
+                    else:
+                        assert cols[slot] == -1 and mp[slot] == -1
+        assert sptr[-1] == total == cols.size
+
+
+def pin_sell_spmv_matches_csr_and_eigen():
+    for (rp, ci, v), n in ((synth.random_csr(500, 300, 41, "f64", 0, 20, 0.1, True), 300),
+                           (synth.powerlaw_csr(2000, 1500, 42, "f64"), 1500)):
+        x = synth.uniform(n, 43, "f64").numpy()
+        ref = oracle.csr_spmv(rp, ci, v, x)
+        for sigma in (1, 128):
+            perm, slen, sptr, cols, mp = oracle.csr_to_sell(rp, ci, 32, sigma)
+            sv = np.where(mp >= 0, v.numpy()[np.maximum(mp, 0)], 0.0)
+            y = oracle.sell_spmv(perm, slen, sptr, cols, sv, x, rp.numel() - 1)
+            assert np.array_equal(y, ref)             # same entries, same order per row
+    N = 30
+    rp, ci, v = synth.laplacian_2d(N)
+    x, lam = _eig2(N, 2, 9)
+    perm, slen, sptr, cols, mp = oracle.csr_to_sell(rp, ci, 32, 64)
+    sv = np.where(mp >= 0, v.numpy()[np.maximum(mp, 0)], 0.0)
+    y = oracle.sell_spmv(perm, slen, sptr, cols, sv, x, N * N)
+    assert np.max(np.abs(y - lam * x)) <= 1e-13
+
+
 # ---- derivatives --------------------------------------------------------------------
 
 def pin_dense_outer_fd():
@@ -452,6 +508,7 @@ PINS = [
     pin_gemv_linearity_and_entries,
     pin_spmv_golden, pin_spmv_laplacian_ones, pin_spmv_eigen_2d, pin_spmv_eigen_3d,
     pin_spmv_dense_bruteforce, pin_spmv_rows, pin_csc_transpose,
+    pin_sell_layout_bruteforce, pin_sell_spmv_matches_csr_and_eigen,
     pin_dense_outer_fd, pin_sampled_outer_fd, pin_scale_dot_gradient,
     pin_round_bf16, pin_round_f16, pin_round_f32,
 ]

@@ -48,6 +48,10 @@ MUTANTS = [
      "double quantum = (exp_unb < -14) ? ldexp(1.0, -23)"),
     ("f16_widen_bias", "else v = ldexp((double)(1024 + f), e - 25);",
      "else v = ldexp((double)(1024 + f), e - 24);"),
+    ("sell_tie_order", "if (lo > lr || (lo == lr && (o >= 0 ? o : m + q) < (r >= 0 ? r : m + p))) break;",
+     "if (lo > lr || (lo == lr && (o >= 0 ? o : m + q) > (r >= 0 ? r : m + p))) break;"),
+    ("sell_row_major_slot", "int64_t slot = slice_ptr[s] + j * C + r;\n                if (j < l) {",
+     "int64_t slot = slice_ptr[s] + r * slice_len[s] + j;\n                if (j < l) {"),
 ]
 
 
