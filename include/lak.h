@@ -324,6 +324,42 @@ LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_
                             void *stream);
 
 /* ------------------------------------------------------------------------
+ * SELL-C-sigma (sliced ELLPACK, C = 32): a format variant of the CSR product
+ * (an extension of this library; the paper leaves sparse formats out, Sec. 1).
+ * Rows are ordered by decreasing length within windows of `sigma` rows
+ * (sigma = 1: no reordering; else a multiple of 32, at most 4096), ties by row
+ * index; position p holds original row perm[p] (-1 past the last row);
+ * positions are padded to mp = 32 * ceil(m / 32).  Slice s (positions
+ * 32s..32s+31) is padded to its longest row, slice_len[s] entries per row,
+ * stored column-major from slice_ptr[s]: entry j of the row at position
+ * 32s + r is slot slice_ptr[s] + 32j + r.  cols[slot] is the column or -1
+ * (padding); map[slot] the CSR position or -1.  The product runs one warp per
+ * slice with coalesced 32-slot loads and adds each row in its CSR order.
+ * Conversion, one time per pattern:
+ *   1. csr_to_sell_count writes perm (mp), slice_len (mp/32) and slice_ptr
+ *      (mp/32 + 1; slice_ptr[mp/32] = total slots);
+ *   2. with total read back, csr_to_sell_fill writes cols and map (total each);
+ *   3. sell_pack_values puts CSR values into SELL slots (again whenever the
+ *      values change).
+ * ---------------------------------------------------------------------- */
+LAK_API lak_status csr_to_sell_count(const int32_t *row_ptr, int64_t m, int32_t sigma,
+                                     int32_t *perm, int32_t *slice_len, int64_t *slice_ptr,
+                                     void *stream);
+LAK_API lak_status csr_to_sell_fill(const int32_t *row_ptr, const int32_t *col_idx, int64_t m,
+                                    const int32_t *perm, const int32_t *slice_len,
+                                    const int64_t *slice_ptr, int32_t *cols, int32_t *map,
+                                    void *stream);
+LAK_API lak_status sell_pack_values(void *sell_vals, const void *csr_vals, const int32_t *map,
+                                    int64_t total, lak_dtype dtype, void *stream);
+/* y[perm[p]] = sum over the row at position p, for the m rows.  cfg: block
+ * (warps of it each take a slice), grid (0 = one warp per slice), vec (slots
+ * loaded per lane per step), increment; NULL = (256, 0, 4, global). */
+LAK_API lak_status sell_spmv(void *y, const int64_t *slice_ptr, const int32_t *slice_len,
+                             const int32_t *perm, const int32_t *cols, const void *vals,
+                             const void *x, int64_t m, lak_dtype dtype, const lak_cfg *cfg,
+                             void *stream);
+
+/* ------------------------------------------------------------------------
  * Reverse-mode building blocks for the products above (an extension of this
  * library; the paper studies forward operations only).  For y = A x:
  * dA = dy x^T (dense_outer; on a CSR pattern csr_sampled_outer) and

@@ -29,6 +29,7 @@ EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_reso
            "dense_gemv_workspace", "dense_gemv", "dense_gemv_axpby", "dense_gemv_trans",
            "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose_workspace", "csr_transpose", "vec_gather", "vec_scale_dev",
+           "csr_to_sell_count", "csr_to_sell_fill", "sell_pack_values", "sell_spmv",
            "lak_batch_plan", "lak_batch_run")
 
 
@@ -112,6 +113,10 @@ _SIGNATURES = {
     "csr_transpose": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P, _SZ, _P]),
     "vec_gather": (_I32, [_P, _P, _P, _I64, _I32, _P]),
     "vec_scale_dev": (_I32, [_P, _P, _P, _I64, _I32, _P]),
+    "csr_to_sell_count": (_I32, [_P, _I64, _I32, _P, _P, _P, _P]),
+    "csr_to_sell_fill": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "sell_pack_values": (_I32, [_P, _P, _P, _I64, _I32, _P]),
+    "sell_spmv": (_I32, [_P, _P, _P, _P, _P, _P, _P, _I64, _I32, _CFGP, _P]),
     "lak_batch_plan": (_I32, [_I32, _I32, _P, _I64, _CFGP, _P, _SZ, ctypes.POINTER(BatchInfo)]),
     "lak_batch_run": (_I32, [ctypes.POINTER(BatchInfo), _P, _P, _SZ, _P]),
 }
