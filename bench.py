@@ -706,6 +706,62 @@ def run_fused(device, reps=20):
     return out
 
 
+def run_formats(device, reps=20):
+    """CSR vs SELL-C-sigma (C = 32) on the sweep's two matrices (3D Laplacian
+    128^3 with sigma = 1, power-law 2M rows with sigma = 1024), FP32 and FP64,
+    L2 flushed (256 MB read) before every timed launch; SELL bytes count the
+    padded slots it actually reads.  Conversion time is reported once."""
+    import time
+
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300.sell import SellMatrix
+
+    dev = device
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+    for storage in ("f32", "f64"):
+        es = 8 if storage == "f64" else 4
+        for name, make, ncols, sigma in (
+                ("lap3d_128", lambda: synth.laplacian_3d(128, storage), 128 ** 3, 1),
+                ("powerlaw_2m", lambda: synth.powerlaw_csr(2_000_000, 2_000_000, 1, storage),
+                 2_000_000, 1024)):
+            rp, ci, v = make()
+            rpd, cid, vd = rp.to(dev), ci.to(dev), v.to(dev)
+            m, nnz = rp.numel() - 1, v.numel()
+            x = synth.device_uniform_(torch.empty(ncols, dtype=vd.dtype, device=dev), 1201)
+            y = torch.empty(m, dtype=vd.dtype, device=dev)
+            csr_bytes = nnz * (es + 4) + (m + 1) * 4 + ncols * es + m * es
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = SellMatrix(rpd, cid, vd, ncols, sigma=sigma)
+            torch.cuda.synchronize()
+            conv_ms = (time.perf_counter() - t0) * 1e3
+            ns = (m + 31) // 32
+            sell_bytes = A.total * (es + 4) + ns * 12 + (m + 31) // 32 * 32 * 4 + ncols * es + m * es
+            best = None
+            for cfg in ((256, 0, 4, 0), (128, 0, 8, 0), (512, 0, 2, 0), (256, 0, 8, 0)):
+                f = (lambda c=cfg: A.spmv(x, y=y, cfg=c))
+                f()
+                t = _median_ms(f, reps, flush)
+                if best is None or t < best[0]:
+                    best = (t, cfg)
+            fc = (lambda: lak.csr_spmv(rpd, cid, vd, x, y=y))
+            fc()
+            tc = _median_ms(fc, reps, flush)
+            out[f"{name}_{storage}"] = {
+                "csr_us": round(tc * 1e3, 2), "csr_GBs": round(csr_bytes / (tc * 1e-3) / 1e9, 1),
+                "sell_us": round(best[0] * 1e3, 2), "sell_cfg": list(best[1]),
+                "sell_GBs_csr_bytes": round(csr_bytes / (best[0] * 1e-3) / 1e9, 1),
+                "sell_padding": round(A.total / max(nnz, 1) - 1, 4), "sigma": sigma,
+                "speedup_vs_csr": round(tc / best[0], 3), "conversion_ms": round(conv_ms, 2),
+                "sell_bytes_read": sell_bytes}
+            del A
+    return out
+
+
 def recorded_traffic(path, name):
     """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
     when there is no record or the kernel's source changed since the capture."""
@@ -988,6 +1044,9 @@ def run_gb300(args):
     fused = None
     if not args.no_fused and not args.only and rank == 0:
         fused = run_fused(device)
+    formats = None
+    if not args.no_formats and not args.only and rank == 0:
+        formats = run_formats(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1016,6 +1075,8 @@ def run_gb300(args):
         line["autograd"] = autograd
     if fused is not None:
         line["fused"] = fused
+    if formats is not None:
+        line["spmv_formats"] = formats
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -1088,6 +1149,8 @@ def main(argv=None):
                     help="skip the forward/backward (differentiation) report")
     ap.add_argument("--no-fused", action="store_true",
                     help="skip the fused-vs-separate report")
+    ap.add_argument("--no-formats", action="store_true",
+                    help="skip the CSR-vs-SELL report")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")

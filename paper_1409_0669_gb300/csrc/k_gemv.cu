@@ -35,6 +35,17 @@ __device__ __forceinline__ T gemv_epilogue(typename Acc<T>::type t, typename Acc
     return narrow<T>(fma_acc(alpha, t, beta * widen(*yold)));
 }
 
+// the same with the old y value already loaded (prefetched before the row's
+// dot product, so the epilogue adds no dependent load)
+template <typename T>
+__device__ __forceinline__ T gemv_epilogue_v(typename Acc<T>::type t, typename Acc<T>::type alpha,
+                                             typename Acc<T>::type beta,
+                                             typename Acc<T>::type yold) {
+    using Ac = typename Acc<T>::type;
+    if (beta == Ac(0)) return narrow<T>(alpha * t);
+    return narrow<T>(fma_acc(alpha, t, beta * yold));
+}
+
 template <typename T, int V>
 __global__ void __launch_bounds__(512)
 gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict__ x, int64_t m,
@@ -63,6 +74,8 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         Ac acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = Ac(0);
+        Ac yold = Ac(0);
+        if (beta != Ac(0) && lg == 0 && row < row_end) yold = widen(y[row]);
         if (row < row_end) row_group_dot<T, V>(acc, A + row * lda, x, n, lg, G);
 #pragma unroll
         for (int w = 1; w < V; w <<= 1) {
@@ -72,7 +85,7 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         Ac s = acc[0];
         if (G <= 32) {
             s = group_sum(s, G);
-            if (lg == 0 && row < row_end) y[row] = gemv_epilogue<T>(s, alpha, beta, y + row);
+            if (lg == 0 && row < row_end) y[row] = gemv_epilogue_v<T>(s, alpha, beta, yold);
         } else {
             s = group_sum(s, 32);
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -81,7 +94,7 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
                 const int wpg = G >> 5;
                 Ac t = Ac(0);
                 for (int w = 0; w < wpg; ++w) t += red[grp * wpg + w];
-                y[row] = gemv_epilogue<T>(t, alpha, beta, y + row);
+                y[row] = gemv_epilogue_v<T>(t, alpha, beta, yold);
             }
             __syncthreads();
         }

@@ -48,7 +48,7 @@ axpby_strided_kernel(T *x, int64_t incx, typename Acc<T>::type alpha, const T *y
 // type), reduced like dot_kernel: per-thread accumulators, warp shuffles, FP64
 // block partials, last block combines in block order.
 template <typename T, int V>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)     // two 512-thread blocks per SM
 axpy_norm2_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, void *out,
                   int64_t n, int64_t head, int64_t nchunks, int inc, unsigned int *counter,
                   double *partials) {
