@@ -762,6 +762,81 @@ def run_formats(device, reps=20):
     return out
 
 
+def run_profile_set(device):
+    """Every kernel family once, at sizes above L2 but a small device footprint
+    (~1.5 GB), for an ncu capture of all of them in one command.  Prints one
+    JSON line mapping each launch (in order) to its algorithmic bytes."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300 import autograd as ag
+    from paper_1409_0669_gb300 import batch as B
+    from paper_1409_0669_gb300.sell import SellMatrix
+
+    dev = device
+    launches = []
+
+    def rec(name, nbytes, fn):
+        fn()
+        launches.append({"name": name, "bytes": int(nbytes)})
+
+    n = 50_000_000
+    y = synth.device_uniform_(torch.empty(n, device=dev), 1301)
+    z = synth.device_uniform_(torch.empty(n, device=dev), 1302)
+    x = torch.empty_like(y)
+    ws = torch.zeros(64 << 20, dtype=torch.uint8, device=dev)
+    out = torch.zeros(1, device=dev)
+    rec("copy_f32", 8 * n, lambda: lak.vec_copy(x, y))
+    rec("axpy_f32", 12 * n, lambda: lak.vec_axpy(x, y, z, 0.5))
+    rec("dot_f32", 8 * n, lambda: lak.vec_dot(y, z, workspace=ws))
+    rec("dot_compensated_f32", 8 * n, lambda: lak.vec_dot_compensated(y, z, workspace=ws))
+    rec("axpby_f32", 12 * n, lambda: lak.vec_axpby(x, 0.5, y, -1.5, z))
+    rec("axpy_norm2_f32", 12 * n, lambda: lak.vec_axpy_norm2(x, y, z, 0.5, workspace=ws))
+    rec("scale_dev_f32", 8 * n, lambda: lak.vec_scale_dev(y, out.fill_(2.0), out=x))
+    rec("dot_noalloc_f32", 8 * n, lambda: lak.vec_dot_noalloc(y, z))
+    g = 8192
+    A = synth.device_normal_(torch.empty(g, g, device=dev), 1303)
+    xg = synth.device_uniform_(torch.empty(g, device=dev), 1304)
+    yg = torch.empty(g, device=dev)
+    gb = (g * g + 2 * g) * 4
+    rec("gemv_row_f32", gb, lambda: lak.dense_gemv(A, xg, y=yg))
+    rec("gemv_col_f32", gb, lambda: lak.dense_gemv(A.t(), xg, y=yg, workspace=ws))
+    rec("gemv_axpby_row_f32", gb + 8 * g, lambda: lak.dense_gemv(A, xg, y=yg, alpha=2.0, beta=1.0))
+    rec("dense_outer_f32", gb, lambda: lak.dense_outer(xg, yg, out=A))
+    A64 = synth.device_normal_(torch.empty(g // 2, g, dtype=torch.float64, device=dev), 1305)
+    x64 = synth.device_uniform_(torch.empty(g, dtype=torch.float64, device=dev), 1306)
+    rec("gemv_row_f64", (g // 2 * g + g + g // 2) * 8, lambda: lak.dense_gemv(A64, x64))
+    del A, A64
+    for nm, (rp, ci, v), nc, sig in (
+            ("lap3d_128", synth.laplacian_3d(128, "f32"), 128 ** 3, 1),
+            ("powerlaw_2m", synth.powerlaw_csr(2_000_000, 2_000_000, 1, "f32"), 2_000_000, 1024)):
+        rpd, cid, vd = rp.to(dev), ci.to(dev), v.to(dev)
+        m, nnz = rp.numel() - 1, v.numel()
+        xs = synth.device_uniform_(torch.empty(nc, device=dev), 1307)
+        ys = torch.empty(m, device=dev)
+        sb = nnz * 8 + (m + 1) * 4 + nc * 4 + m * 4
+        rec(f"spmv_csr_{nm}_f32", sb, lambda: lak.csr_spmv(rpd, cid, vd, xs, y=ys))
+        S = SellMatrix(rpd, cid, vd, nc, sigma=sig)
+        rec(f"spmv_sell_{nm}_f32", sb, lambda: S.spmv(xs, y=ys))
+        dv = torch.empty(nnz, device=dev)
+        rec(f"sampled_outer_{nm}_f32", nnz * 8 + (m + 1) * 4 + nc * 4 + m * 4,
+            lambda: lak.csr_sampled_outer(rpd, cid, ys, xs, out=dv))
+        pat = ag.CsrPattern(rpd, cid, nc)
+        cp, ri, perm = pat.transpose()
+        rec(f"gather_{nm}_f32", nnz * 12, lambda: lak.vec_gather(vd, perm, out=dv))
+        del S
+    ns = synth.log_uniform_ints(512, 65_536, 1_048_576, 1308)
+    bx = [torch.empty(int(k), device=dev) for k in ns]
+    byy = [synth.device_uniform_(torch.empty(int(k), device=dev), 1309) for k in ns]
+    bz = [synth.device_uniform_(torch.empty(int(k), device=dev), 1310) for k in ns]
+    bt = B.axpy_batch(bx, byy, bz, [0.5] * len(ns))
+    rec("batch_axpy_f32", 12 * int(sum(int(k) for k in ns)), bt.run)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_set": launches}))
+    return 0
+
+
 def recorded_traffic(path, name):
     """DRAM bytes per launch recorded by an ncu capture of this kernel, or None
     when there is no record or the kernel's source changed since the capture."""
@@ -1151,6 +1226,8 @@ def main(argv=None):
                     help="skip the fused-vs-separate report")
     ap.add_argument("--no-formats", action="store_true",
                     help="skip the CSR-vs-SELL report")
+    ap.add_argument("--profile-set", action="store_true",
+                    help="launch every kernel family once at a small footprint (for ncu)")
     ap.add_argument("--only", default=None,
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")
@@ -1162,6 +1239,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_set:
+        import torch
+        torch.cuda.set_device(0)
+        return run_profile_set(torch.device("cuda", 0))
     return run_gb300(args)
 
 
