@@ -546,14 +546,14 @@ def run_batched(device, reps=10, count=4096, seed=4000):
             bt.run()
         separate(calls)
         torch.cuda.synchronize()
-        t_b = _median_ms(bt.run, reps)
-        t_s = _median_ms(lambda: separate(calls), max(3, reps // 3))
+        t_b = _launch_ms(bt.run, reps)
+        t_s = _launch_ms(lambda: separate(calls), max(3, reps // 3))
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             separate_graph_calls = [(fn, a[:-1] + (torch.cuda.current_stream().cuda_stream,))
                                     for fn, a in calls]
             separate(separate_graph_calls)
-        t_g = _median_ms(g.replay, reps)
+        t_g = _launch_ms(g.replay, reps)
         del g
         report[name] = {"bytes": nbytes, "units": bt.total_units,
                         "us_batched": round(t_b * 1e3, 1),
@@ -567,7 +567,7 @@ def run_batched(device, reps=10, count=4096, seed=4000):
     with torch.cuda.graph(g):
         for bt, _, _ in fams.values():
             bt.run()
-    t_all = _median_ms(g.replay, reps)
+    t_all = _launch_ms(g.replay, reps)
     tot = sum(nb for _, _, nb in fams.values())
     report["all_families_one_graph"] = {"bytes": tot, "us": round(t_all * 1e3, 1),
                                         "GBs": round(tot / (t_all * 1e-3) / 1e9, 1)}
@@ -593,7 +593,7 @@ def run_autograd(device, reps=20):
     def rec(name, fn, nbytes):
         for _ in range(3):
             fn()
-        ms = _median_ms(fn, reps, flush)
+        ms = _launch_ms(fn, reps, flush)
         out[name] = {"us": round(ms * 1e3, 2), "GBs": round(nbytes / (ms * 1e-3) / 1e9, 1)}
 
     m = n = 4096
@@ -668,7 +668,9 @@ def run_fused(device, reps=20):
         y = synth.device_uniform_(torch.empty(n, dtype=dt, device=dev), 1101)
         z = synth.device_uniform_(torch.empty(n, dtype=dt, device=dev), 1102)
         x = torch.empty_like(y)
-        ws = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+        ws = torch.zeros(max(lak.vec_dot_workspace(n, storage),
+                             lak.vec_axpy_norm2_workspace(n, storage)),
+                         dtype=torch.uint8, device=dev)
 
         def fused():
             lak.vec_axpy_norm2(x, y, z, 0.5, workspace=ws)
@@ -678,8 +680,8 @@ def run_fused(device, reps=20):
             lak.vec_dot(x, x, workspace=ws)
         for f in (fused, separate):
             f()
-        tf = _median_ms(fused, reps, flush)
-        ts = _median_ms(separate, reps, flush)
+        tf = _launch_ms(fused, reps, flush)
+        ts = _launch_ms(separate, reps, flush)
         out[f"axpy_norm2_{storage}"] = {"us_fused": round(tf * 1e3, 1),
                                         "GBs_fused": round(3 * n * es / (tf * 1e-3) / 1e9, 1),
                                         "us_separate": round(ts * 1e3, 1),
@@ -698,8 +700,8 @@ def run_fused(device, reps=20):
             lak.vec_axpby(yg, -1.0, yg, 0.5, tmp)
         for f in (gfused, gseparate):
             f()
-        tf = _median_ms(gfused, reps, flush)
-        ts = _median_ms(gseparate, reps, flush)
+        tf = _launch_ms(gfused, reps, flush)
+        ts = _launch_ms(gseparate, reps, flush)
         out[f"gemv_axpby_{storage}"] = {"us_fused": round(tf * 1e3, 1), "us_separate": round(ts * 1e3, 1),
                                         "speedup": round(ts / tf, 3)}
         del y, z, x, A
@@ -745,12 +747,12 @@ def run_formats(device, reps=20):
             for cfg in ((256, 0, 4, 0), (128, 0, 8, 0), (512, 0, 2, 0), (256, 0, 8, 0)):
                 f = (lambda c=cfg: A.spmv(x, y=y, cfg=c))
                 f()
-                t = _median_ms(f, reps, flush)
+                t = _launch_ms(f, reps, flush)
                 if best is None or t < best[0]:
                     best = (t, cfg)
             fc = (lambda: lak.csr_spmv(rpd, cid, vd, x, y=y))
             fc()
-            tc = _median_ms(fc, reps, flush)
+            tc = _launch_ms(fc, reps, flush)
             out[f"{name}_{storage}"] = {
                 "csr_us": round(tc * 1e3, 2), "csr_GBs": round(csr_bytes / (tc * 1e-3) / 1e9, 1),
                 "sell_us": round(best[0] * 1e3, 2), "sell_cfg": list(best[1]),
@@ -857,22 +859,15 @@ def recorded_traffic(path, name):
     return rec["dram_bytes"]
 
 
-def _median_ms(fn, reps, flush=None):
-    """Median CUDA-event time of `fn`; `flush` (a buffer larger than L2) is read
-    before each launch, which evicts L2 without leaving dirty lines behind."""
-    import torch
-    ts = []
-    for _ in range(reps):
-        if flush is not None:
-            flush.sum()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        b.record()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    return statistics.median(ts)
+def _launch_ms(fn, reps, flush=None):
+    """Device time of one call of `fn` in ms (CUDA events on the current
+    stream).  With `flush` (a buffer larger than L2, read before every call to
+    evict L2 without leaving dirty lines): the calls and flushes run back to
+    back in one event interval and the flushes' own time is subtracted --
+    GB300's event clock ticks in ~2 us steps, too coarse for one short launch.
+    Without: the trimmed mean of per-call intervals."""
+    from paper_1409_0669_gb300.timing import launch_time_us
+    return launch_time_us(fn, reps, flush) * 1e-3
 
 
 def run_precision(device, reps=20):
@@ -933,7 +928,9 @@ def run_precision(device, reps=20):
         rp_l, ci_l, v_l = lap[0].to(dev), lap[1].to(dev), lap[2].to(dev).to(dt)
         rp_p, ci_p, v_p = pl[0].to(dev), pl[1].to(dev), pl[2].to(dev).to(dt)
         xl, xp = xl32.to(dt), xp32.to(dt)
-        ws = torch.zeros(1 << 22, dtype=torch.uint8, device=dev)
+        ws = torch.zeros(max(lak.vec_dot_workspace(n, storage),
+                             lak.dense_gemv_workspace(g, g, "col", storage), 256),
+                         dtype=torch.uint8, device=dev)
         yo = torch.empty(g, dtype=dt, device=dev)
         sl = torch.empty(rp_l.numel() - 1, dtype=dt, device=dev)
         sp = torch.empty(rp_p.numel() - 1, dtype=dt, device=dev)
@@ -950,7 +947,7 @@ def run_precision(device, reps=20):
         for name, (fn, nbytes) in cases.items():
             for _ in range(3):
                 fn()
-            ms = _median_ms(fn, reps, flush)
+            ms = _launch_ms(fn, reps, flush)
             # error of this launch's result
             if name == "axpy":
                 fn()
@@ -978,7 +975,7 @@ def run_precision(device, reps=20):
     # compensated vs plain inner product on mixed magnitudes
     a = synth.device_mixed_magnitude_(torch.empty(n, device=dev), 908)
     b = synth.device_mixed_magnitude_(torch.empty(n, device=dev), 909)
-    ws = torch.zeros(1 << 22, dtype=torch.uint8, device=dev)
+    ws = torch.zeros(lak.vec_dot_workspace(n, "f32"), dtype=torch.uint8, device=dev)
     ah, bh = a.cpu(), b.cpu()
     r = oracle.dot(ah, bh)
     abs_sum = float(np.abs(ah.double().numpy() * bh.double().numpy()).sum())
@@ -988,7 +985,7 @@ def run_precision(device, reps=20):
                       ("compensated_f32", lambda: lak.vec_dot_compensated(a, b, workspace=ws))):
         for _ in range(3):
             fn()
-        ms = _median_ms(fn, reps, flush)
+        ms = _launch_ms(fn, reps, flush)
         v = fn().item()
         comp[label] = {"us": round(ms * 1e3, 2), "GBs": round(2 * n * 4 / (ms * 1e-3) / 1e9, 1),
                        "rel_err": abs(v - r) / abs(r), "err_over_abs_sum": abs(v - r) / abs_sum}

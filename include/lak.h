@@ -96,10 +96,10 @@ typedef enum {
  *              GEMV gives each thread `vec` consecutive rows; CSR SpMV issues
  *              `vec` independent nonzero loads per thread per step.
  *   increment  LAK_INC_GLOBAL or LAK_INC_LOCAL (ignored when block = 0)
- * A NULL cfg, or one whose block is 0, takes the library default for the op
- * and storage type (set by lak_set_default_cfg, e.g. from an autotuning
- * cache, else built in); a zero grid or vec in an otherwise explicit cfg is
- * filled in by the library.
+ * A NULL cfg, or one whose block is 0, takes the library default for the op,
+ * storage type and size bucket (set by lak_set_default_cfg[_bucket], e.g. from
+ * an autotuning cache, else built in); a zero grid or vec in an otherwise
+ * explicit cfg is filled in by the library.
  */
 typedef struct {
     int32_t block;
@@ -115,10 +115,34 @@ LAK_API const char *lak_last_error(void);
 LAK_API int32_t lak_abi_version(void);
 
 /*
- * Replace the default configuration used for (op, dtype) when a call passes
- * no explicit cfg; cfg = NULL restores the built-in default.  Process-wide;
- * not synchronised against concurrent calls that read it.
+ * Size buckets.  Defaults are kept per (op, dtype, size bucket): the bucket is
+ * fixed by the call's algorithmic bytes B (operands read once + results
+ * written; copy/dot 2n*s, axpy 3n*s, dense_gemv (mn + m + n)*s, csr_spmv
+ * nnz*(s + 4) + (m + 1)*4 + (m + n)*s, s = bytes per stored value):
+ *   0: B < 8 MiB    1: B < 64 MiB    2: B < 512 MiB    3: otherwise.
+ * The paper tunes one configuration per device and operation (Sec. 3); on
+ * GB300 the best launch shape for a call that moves a few MB (launch-latency
+ * bound) differs from the one for a call that streams GBs, so the autotuner
+ * fills one entry per bucket.
  */
+#define LAK_SIZE_BUCKETS 4
+
+/*
+ * The size bucket (0 .. LAK_SIZE_BUCKETS-1) a call of `op` with these sizes
+ * falls in (sizes as in lak_resolve_cfg), or a negative lak_status.
+ */
+LAK_API int32_t lak_size_bucket(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz);
+
+/*
+ * Replace the default configuration used for (op, dtype) in size bucket
+ * `bucket` (-1: every bucket) when a call passes no explicit cfg; cfg = NULL
+ * restores the built-in default.  Process-wide; not synchronised against
+ * concurrent calls that read it.
+ */
+LAK_API lak_status lak_set_default_cfg_bucket(lak_op op, lak_dtype dtype, int32_t bucket,
+                                              const lak_cfg *cfg);
+
+/* lak_set_default_cfg_bucket(op, dtype, -1, cfg): every size bucket. */
 LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg);
 
 /*
@@ -428,7 +452,9 @@ LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, in
  * instances), LAK_OP_SPMV (lak_csr_desc, warp-segmented rows).  Per instance
  * the results equal those of the single-instance calls up to the order of
  * floating-point summation (axpy: identical).  The dot keeps at most
- * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).
+ * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).  A NULL cfg
+ * (or block 0) takes the batched kernels' own built-in launch shape, not the
+ * per-size defaults of the single-instance calls.
  * ---------------------------------------------------------------------- */
 typedef struct { void *x; const void *y; const void *z; int64_t n; double alpha; } lak_axpy_desc;
 typedef struct { void *out; const void *x; const void *y; int64_t n; } lak_dot_desc;

@@ -23,10 +23,12 @@ import torch
 from . import _native
 from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
-__all__ = ["vec_copy", "vec_axpy", "vec_axpby", "vec_axpy_norm2", "dense_gemv_trans", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
+__all__ = ["vec_copy", "vec_axpy", "vec_axpby", "vec_axpy_norm2", "vec_axpy_norm2_workspace",
+           "dense_gemv_trans", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
            "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "dense_outer", "csr_sampled_outer",
-           "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg", "Cfg",
+           "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg",
+           "size_bucket", "SIZE_BUCKETS", "Cfg",
            "LakError", "storage_of", "library_path"]
 
 _lib = _native.load()
@@ -125,10 +127,24 @@ def resolve_cfg(op: str, storage: str, m: int, n: int = 0, nnz: int = 0,
     return out
 
 
-def set_default_cfg(op: str, storage: str, cfg: CfgLike):
-    """Replace (or with cfg=None restore) the default configuration of an op."""
+SIZE_BUCKETS = 4
+
+
+def size_bucket(op: str, storage: str, m: int, n: int = 0, nnz: int = 0) -> int:
+    """The size bucket (0..3) of a call with these sizes (lak_size_bucket);
+    sizes as in resolve_cfg."""
+    b = _lib.lak_size_bucket(OPS[op], DTYPES[storage], int(m), int(n), int(nnz))
+    if b < 0:
+        _native.check("lak_size_bucket", b)
+    return b
+
+
+def set_default_cfg(op: str, storage: str, cfg: CfgLike, bucket: Optional[int] = None):
+    """Replace (or with cfg=None restore) the default configuration of an op,
+    in one size bucket or (bucket=None) in all of them."""
+    b = -1 if bucket is None else int(bucket)
     _native.check("lak_set_default_cfg",
-                  _lib.lak_set_default_cfg(OPS[op], DTYPES[storage], _cfg_ptr(cfg)))
+                  _lib.lak_set_default_cfg_bucket(OPS[op], DTYPES[storage], b, _cfg_ptr(cfg)))
 
 
 def vec_copy(x: torch.Tensor, y: torch.Tensor, cfg: CfgLike = None, stream=None) -> torch.Tensor:
@@ -199,6 +215,10 @@ def vec_axpy_norm2(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, alpha: flo
                              workspace.numel(), _cfg_ptr(cfg), sh)
     _native.check("vec_axpy_norm2", st)
     return out
+
+
+def vec_axpy_norm2_workspace(n: int, storage: str, cfg: CfgLike = None) -> int:
+    return int(_lib.vec_axpy_norm2_workspace(int(n), DTYPES[storage], _cfg_ptr(cfg)))
 
 
 def vec_dot_workspace(n: int, storage: str, cfg: CfgLike = None) -> int:

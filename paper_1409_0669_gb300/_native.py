@@ -23,6 +23,7 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 
 # exported symbols, in header order (checked by the ABI test)
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
+           "lak_size_bucket", "lak_set_default_cfg_bucket",
            "vec_copy", "vec_axpy", "vec_axpby", "vec_axpby_strided", "vec_axpy_norm2_workspace",
            "vec_axpy_norm2", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
            "vec_dot_noalloc",
@@ -89,6 +90,8 @@ _SIGNATURES = {
     "lak_last_error": (ctypes.c_char_p, []),
     "lak_abi_version": (_I32, []),
     "lak_set_default_cfg": (_I32, [_I32, _I32, _CFGP]),
+    "lak_set_default_cfg_bucket": (_I32, [_I32, _I32, _I32, _CFGP]),
+    "lak_size_bucket": (_I32, [_I32, _I32, _I64, _I64, _I64]),
     "lak_resolve_cfg": (_I32, [_I32, _I32, _I64, _I64, _I64, _CFGP, _CFGP]),
     "vec_copy": (_I32, [_P, _P, _I64, _I32, _CFGP, _P]),
     "vec_axpy": (_I32, [_P, _P, _P, ctypes.c_double, _I64, _I32, _CFGP, _P]),

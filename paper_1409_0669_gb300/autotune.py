@@ -8,9 +8,17 @@ GB300 the same four axes become:
   block      64, 128, 256, 512 threads
   grid       automatic (enough blocks to cover the data once) or a multiple of
              the SM count (1, 2, 4, 8, 16, 32 blocks per SM: persistent grids)
-Each configuration is timed with CUDA events on the launching stream (median
-of `reps` launches; when the operands fit in L2, a 256 MB buffer is read before
-each launch to evict them).
+Each configuration is timed with CUDA events on the launching stream
+(timing.launch_time_us: operands larger than L2 launch by launch; operands
+that fit in L2 as `reps` (256 MB flush read, launch) pairs in one event
+interval minus the flushes alone -- GB300's event clock ticks in steps of
+about 2 us, too coarse for one launch of a few microseconds).
+
+Defaults are kept per size bucket (lak_size_bucket: the call's algorithmic
+bytes, below 8 MiB / 64 MiB / 512 MiB / above).  `tune_buckets` times every
+configuration at several sizes, groups the sizes by bucket and keeps, per
+bucket, the configuration whose worst ratio to each size's own optimum is
+best.
 
 `copy_first_study` repeats the paper's central experiment (Sec. 3.2, 3.4):
 tune the copy kernel exhaustively, keep the configurations within 15 % of the
@@ -22,18 +30,21 @@ installed as the library's per-op defaults (lak_set_default_cfg).
 
   python -m paper_1409_0669_gb300.autotune --op copy --storage f32 --size 100000000
   python -m paper_1409_0669_gb300.autotune --study --storage f32 --out tune.json
+  python -m paper_1409_0669_gb300.autotune --buckets --op dot --storage f64 \
+      --size 46416,215443,2154435,10000000 --out tune.json
 """
 from __future__ import annotations
 
 import argparse
 import json
-import statistics
 from typing import Callable, Dict, List, Optional
 
 import torch
 
 from . import _native
 from ._native import DTYPES, LakCfg, LakError
+from ._native import OPS as _OP_CODES
+from .timing import launch_time_us
 
 OPS = ("copy", "axpy", "dot", "gemv_row", "gemv_col", "spmv")
 BLOCKS = (64, 128, 256, 512)
@@ -89,6 +100,7 @@ class Problem:
                 self.fn = lambda c: lib.vec_dot(out.data_ptr(), y.data_ptr(), z.data_ptr(), n,
                                                 code, ws.data_ptr(), ws.numel(), c, sh)
             self.footprint = self.nbytes
+            self.dims = (n, n, 0)
         elif op in ("gemv_row", "gemv_col"):
             m = n = int(size)
             A = synth.device_normal_(torch.empty(m * n, dtype=dt, device=self.device), seed + 3)
@@ -102,10 +114,14 @@ class Problem:
                                                n if lay == 0 else m, lay, code, ws.data_ptr(),
                                                ws.numel(), c, sh)
             self.footprint = self.nbytes
+            self.dims = (m, n, 0)
         elif op == "spmv":
             if size == "lap3d_128":
                 rp, ci, v = synth.laplacian_3d(128, storage)
                 ncols = 128 ** 3
+            elif size == "lap3d_64":
+                rp, ci, v = synth.laplacian_3d(64, storage)
+                ncols = 64 ** 3
             elif size == "lap2d_256":
                 rp, ci, v = synth.laplacian_2d(256, storage)
                 ncols = 256 ** 2
@@ -125,6 +141,7 @@ class Problem:
                                              vd.data_ptr(), xs.data_ptr(), m, ncols, nnz, code,
                                              c, sh)
             self.footprint = self.nbytes
+            self.dims = (m, ncols, nnz)
         else:
             raise ValueError(op)
         l2 = torch.cuda.get_device_properties(self.device).L2_cache_size
@@ -132,25 +149,21 @@ class Problem:
             if self.footprint < 2 * l2 else None
 
     def time_cfg(self, cfg: Optional[LakCfg], reps: int = 10, warm: int = 2) -> float:
-        """Median launch time in microseconds (raises LakError on a bad cfg)."""
+        """Device time of one launch in microseconds, L2 cold (raises LakError
+        on a bad cfg)."""
         import ctypes
         cptr = ctypes.byref(cfg) if cfg is not None else None
         for _ in range(warm):
             st = self.fn(cptr)
             _native.check(self.op, st)
-        times = []
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        for _ in range(reps):
-            if self.flush is not None:
-                self.flush.sum()          # evicts L2 without leaving dirty lines
-            ev0.record(self.stream)
+        torch.cuda.synchronize(self.device)
+
+        def call():
             st = self.fn(cptr)
-            ev1.record(self.stream)
-            _native.check(self.op, st)
-            ev1.synchronize()
-            times.append(ev0.elapsed_time(ev1) * 1e3)
-        return statistics.median(times)
+            if st != 0:
+                _native.check(self.op, st)
+
+        return launch_time_us(call, reps, self.flush, self.stream)
 
 
 def tune(op: str, storage: str, size, reps: int = 10, cfgs: Optional[List[LakCfg]] = None,
@@ -166,7 +179,7 @@ def tune(op: str, storage: str, size, reps: int = 10, cfgs: Optional[List[LakCfg
         except LakError:
             continue
         results.append({"cfg": list(c.as_tuple()), "us": us,
-                        "GBs": prob.nbytes / (us * 1e-6) / 1e9})
+                        "GBs": prob.nbytes / (max(us, 1e-3) * 1e-6) / 1e9})
     results.sort(key=lambda r: r["us"])
     return results
 
@@ -210,9 +223,46 @@ def copy_first_study(storage: str, sizes: Dict[str, object], keep_frac: float = 
     return report
 
 
+def problem_bucket(prob: Problem) -> int:
+    """Size bucket of a Problem's call (lak_size_bucket)."""
+    lib = _native.load()
+    return lib.lak_size_bucket(_OP_CODES[prob.op], DTYPES[prob.storage], *prob.dims)
+
+
+def choose_per_bucket(results: Dict[object, List[Dict]], buckets: Dict[object, int]) -> Dict[int, Dict]:
+    """results: size -> tune() output; buckets: size -> bucket.  Per bucket,
+    the configuration (timed at every size of the bucket) whose worst ratio
+    of the size's best time to its own time is largest."""
+    out = {}
+    for b in sorted(set(buckets.values())):
+        sizes = [sz for sz, bb in buckets.items() if bb == b]
+        tables = {sz: {tuple(r["cfg"]): r["us"] for r in results[sz]} for sz in sizes}
+        common = set.intersection(*(set(t) for t in tables.values()))
+        best_cfg, best_score = None, -1.0
+        for c in sorted(common):
+            score = min(min(tables[sz].values()) / tables[sz][c] for sz in sizes)
+            if score > best_score:
+                best_cfg, best_score = c, score
+        if best_cfg is not None:
+            out[b] = {"cfg": list(best_cfg), "worst_ratio": best_score, "sizes": sizes}
+    return out
+
+
+def tune_buckets(op: str, storage: str, sizes, reps: int = 15) -> Dict[int, Dict]:
+    """Tune `op` at every size and keep one configuration per size bucket."""
+    results, buckets = {}, {}
+    for sz in sizes:
+        prob = Problem(op, storage, sz)
+        results[sz] = tune(op, storage, sz, reps, problem=prob)
+        buckets[sz] = problem_bucket(prob)
+        del prob
+        torch.cuda.empty_cache()
+    return choose_per_bucket(results, buckets)
+
+
 def _default_point(prob: Problem, reps: int) -> Dict:
     us = prob.time_cfg(None, reps)
-    return {"us": us, "GBs": prob.nbytes / (us * 1e-6) / 1e9}
+    return {"us": us, "GBs": prob.nbytes / (max(us, 1e-3) * 1e-6) / 1e9}
 
 
 def cache_key() -> str:
@@ -221,7 +271,8 @@ def cache_key() -> str:
 
 
 def save_cache(path: str, entries: Dict[str, List[int]]):
-    """entries: {"<op>:<storage>": [block, grid, vec, increment]}"""
+    """entries: {"<op>:<storage>": [block, grid, vec, increment]} for every
+    size bucket, or {"<op>:<storage>:<bucket>": [...]} for one."""
     try:
         with open(path) as fh:
             data = json.load(fh)
@@ -239,8 +290,9 @@ def apply_cache(path: str) -> int:
         data = json.load(fh)
     entries = data.get(cache_key(), {})
     for key, cfg in entries.items():
-        op, storage = key.split(":")
-        set_default_cfg(op, storage, tuple(cfg))
+        parts = key.split(":")
+        bucket = int(parts[2]) if len(parts) == 3 else None
+        set_default_cfg(parts[0], parts[1], tuple(cfg), bucket)
     return len(entries)
 
 
@@ -252,12 +304,21 @@ def _main(argv=None):
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--top", type=int, default=15)
     ap.add_argument("--study", action="store_true", help="copy-first transfer study")
+    ap.add_argument("--buckets", action="store_true",
+                    help="one configuration per size bucket from the comma-separated --size list")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     size = args.size
     if size.isdigit():
         size = int(size)
-    if args.study:
+    if args.buckets:
+        sizes = [int(v) if v.isdigit() else v for v in args.size.split(",")]
+        per = tune_buckets(args.op, args.storage, sizes, args.reps)
+        text = json.dumps({"op": args.op, "storage": args.storage,
+                           "buckets": {str(b): v for b, v in per.items()},
+                           "cache": {f"{args.op}:{args.storage}:{b}": v["cfg"]
+                                     for b, v in per.items()}}, indent=1)
+    elif args.study:
         sizes = {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
                  "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"}
         rep = copy_first_study(args.storage, sizes, reps=args.reps)

@@ -347,7 +347,7 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
          (cfg->vec != 0 && cfg->vec != 1 && cfg->vec != 2 && cfg->vec != 4 && cfg->vec != 8 &&
           cfg->vec != 16)))
         return fail(LAK_EINVAL, "lak_batch_plan: invalid cfg");
-    const lak_cfg c = base_config(op, dtype, cfg);
+    const lak_cfg c = batch_config(op, dtype, cfg);
     int vec = c.vec;
     if (op == LAK_OP_SPMV) vec = vec < 4 ? 4 : (vec > 8 ? 8 : vec);   // seg rows: 4..8 entries
     const int es = esize(dtype);

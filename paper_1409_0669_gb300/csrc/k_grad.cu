@@ -13,50 +13,67 @@ namespace {
 
 // ---- dense outer product --------------------------------------------------------
 
-// One block row-group per row: the row of dA is dy[i] times x, written with wide
-// stores; x is re-read by every row (L1/L2 resident).
+// Grid (column blocks) x (row groups): each block owns a contiguous range of
+// rows and each thread a V-wide chunk of columns; the thread keeps its chunk
+// of x in registers and writes dy[i] times it into every row of the range, so
+// the row loop holds no dependent global load (dy[i] is one broadcast L1 hit)
+// and is bound by the stores alone.
 template <typename T, int V>
 __global__ void __launch_bounds__(512)
 outer_kernel(T *__restrict__ dA, const T *__restrict__ dy, const T *__restrict__ x, int64_t m,
              int64_t n, int64_t ldd, bool vec_ok) {
     using A = typename Acc<T>::type;
-    for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
-        const A d = widen(dy[i]);
-        T *row = dA + i * ldd;
-        if (vec_ok) {
-            const int64_t nch = n / V;
-            for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
-                 c += (int64_t)gridDim.x * blockDim.x) {
-                Pack<T, V> px, po;
-                load_pack<T, V, CACHED>(px, x + c * V);
+    const int64_t rows_per = (m + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+    const int64_t r1 = r0 + rows_per < m ? r0 + rows_per : m;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tstride = (int64_t)gridDim.x * blockDim.x;
+    if (vec_ok) {
+        const int64_t nch = n / V;
+        for (int64_t c = t; c < nch; c += tstride) {
+            Pack<T, V> px;
+            load_pack<T, V, CACHED>(px, x + c * V);
+            A xv[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) po.e[v] = narrow<T>(d * widen(px.e[v]));
-                store_pack<T, V>(row + c * V, po);
+            for (int v = 0; v < V; ++v) xv[v] = widen(px.e[v]);
+#pragma unroll 4
+            for (int64_t i = r0; i < r1; ++i) {
+                const A d = widen(__ldg(dy + i));
+                Pack<T, V> po;
+#pragma unroll
+                for (int v = 0; v < V; ++v) po.e[v] = narrow<T>(d * xv[v]);
+                store_pack<T, V>(dA + i * ldd + c * V, po);
             }
-            for (int64_t j = nch * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-                 j += (int64_t)gridDim.x * blockDim.x)
-                row[j] = narrow<T>(d * widen(x[j]));
-        } else {
-            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-                 j += (int64_t)gridDim.x * blockDim.x)
-                row[j] = narrow<T>(d * widen(x[j]));
+        }
+        for (int64_t j = nch * V + t; j < n; j += tstride) {
+            const A xj = widen(x[j]);
+            for (int64_t i = r0; i < r1; ++i) dA[i * ldd + j] = narrow<T>(widen(dy[i]) * xj);
+        }
+    } else {
+        for (int64_t j = t; j < n; j += tstride) {
+            const A xj = widen(x[j]);
+            for (int64_t i = r0; i < r1; ++i) dA[i * ldd + j] = narrow<T>(widen(dy[i]) * xj);
         }
     }
 }
 
 // ---- CSR sampled outer product ------------------------------------------------------
 
-template <typename T>
+// A group of G lanes per row (G from the mean row length): the lanes of a
+// group write consecutive entries of the row, so the stores and the col_idx
+// loads of a warp stay contiguous.
+template <typename T, int G>
 __global__ void __launch_bounds__(512)
 sampled_outer_kernel(T *__restrict__ dvals, const int32_t *__restrict__ rp,
                      const int32_t *__restrict__ ci, const T *__restrict__ dy,
                      const T *__restrict__ x, int64_t m) {
     using A = typename Acc<T>::type;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int lg = threadIdx.x % G;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < m; i += groups) {
         const A d = widen(dy[i]);
         const int64_t k1 = __ldg(rp + i + 1);
-        for (int64_t k = __ldg(rp + i); k < k1; ++k)
+        for (int64_t k = __ldg(rp + i) + lg; k < k1; k += G)
             dvals[k] = narrow<T>(d * widen(ld_cached(x + __ldg(ci + k))));
     }
 }
@@ -206,11 +223,18 @@ lak_status outer_t(void *dA, const void *dy, const void *x, int64_t m, int64_t n
     const int w = V * (int)sizeof(T);
     const bool vec_ok = (uintptr_t)dA % w == 0 && (uintptr_t)x % w == 0 &&
                         (ldd * (int64_t)sizeof(T)) % w == 0;
+    // a few column blocks per row, and enough row groups to fill the GPU about
+    // twice; every block then walks many rows (long-lived blocks)
     const int block = 256;
     int64_t gx = (n / V + block - 1) / block;
     if (gx < 1) gx = 1;
     if (gx > 64) gx = 64;
-    int64_t gy = m < 65535 ? m : 65535;
+    const DeviceInfo *di = device_info();
+    const int64_t cap = di ? 2LL * di->sms * (di->max_threads_per_sm / block) : 2048;
+    int64_t gy = cap / gx;
+    if (gy < 1) gy = 1;
+    if (gy > m) gy = m;
+    if (gy > 65535) gy = 65535;
     outer_kernel<T, V><<<dim3((unsigned)gx, (unsigned)gy), block, 0, s>>>(
         static_cast<T *>(dA), static_cast<const T *>(dy), static_cast<const T *>(x), m, n, ldd,
         vec_ok);
@@ -253,11 +277,22 @@ LAK_API lak_status csr_sampled_outer(void *dvals, const int32_t *row_ptr, const 
         return fail(LAK_EINVAL, "csr_sampled_outer: NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     const int block = 256;
-    const int grid = grid_for(m, block);
-#define LAK_SO(T)                                                                            \
-    sampled_outer_kernel<T><<<grid, block, 0, s>>>(static_cast<T *>(dvals), row_ptr, col_idx,  \
-                                                   static_cast<const T *>(dy),               \
-                                                   static_cast<const T *>(x), m)
+    const int64_t mean = (nnz + m - 1) / m;
+    // short rows (stencils): a thread per row reads its few col_idx from one
+    // cache line; longer rows: a group of about half the mean row length
+    const int G = mean <= 12 ? 1 : mean <= 16 ? 8 : mean <= 32 ? 16 : 32;
+    const int grid = grid_for(m * G, block);
+#define LAK_SOG(T, GG)                                                                         \
+    sampled_outer_kernel<T, GG><<<grid, block, 0, s>>>(static_cast<T *>(dvals), row_ptr, col_idx, \
+                                                       static_cast<const T *>(dy),              \
+                                                       static_cast<const T *>(x), m)
+#define LAK_SO(T)                     \
+    switch (G) {                      \
+    case 1: LAK_SOG(T, 1); break;     \
+    case 8: LAK_SOG(T, 8); break;     \
+    case 16: LAK_SOG(T, 16); break;   \
+    default: LAK_SOG(T, 32); break;   \
+    }
     switch (dtype) {
     case LAK_F32: LAK_SO(float); break;
     case LAK_F64: LAK_SO(double); break;
@@ -265,6 +300,7 @@ LAK_API lak_status csr_sampled_outer(void *dvals, const int32_t *row_ptr, const 
     case LAK_F16: LAK_SO(__half); break;
     }
 #undef LAK_SO
+#undef LAK_SOG
     return check_launch("csr_sampled_outer");
 }
 

@@ -77,26 +77,96 @@ const DeviceInfo *device_info() {
 
 namespace {
 
-// Built-in defaults per op, measured on GB300 with the autotuner (every
-// combination of block 64..512, grid 1..32 blocks per SM or automatic, vec
-// 1..16 and both increments, at the largest sweep size).  Like the paper's GPU
-// guideline (Sec. 4) they favour many work-groups and the global increment;
-// unlike it, wide per-thread accesses pay off on GB300 (32-64 bytes in flight
-// per thread).  `bytes` is the per-thread access width, turned into a vector
-// length for the storage type; the grid is stored per SM.
-struct DefaultCfg {
-    int block, grid_per_sm, bytes, inc;
-};
+// Size buckets: a call's algorithmic bytes (operands read + results written)
+// select one of LAK_SIZE_BUCKETS default configurations.  Below ~8 MB a call
+// is launch-latency bound, up to ~64 MB (the paper's own problem sizes on a
+// 7 TB/s part) the DRAM latency and the ramp of the first wave still show, and
+// from ~512 MB on the launch streams at the bandwidth ceiling.
+constexpr int64_t kBucketBound[LAK_SIZE_BUCKETS - 1] = {8LL << 20, 64LL << 20, 512LL << 20};
 
-DefaultCfg default_row(lak_op op, lak_dtype dt) {
+int64_t op_bytes(lak_op op, lak_dtype dt, int64_t m, int64_t n, int64_t nnz) {
+    const int64_t es = esize(dt);
     switch (op) {
     case LAK_OP_COPY:
-    case LAK_OP_AXPY: return {512, 32, 64, LAK_INC_GLOBAL};
-    case LAK_OP_DOT: return {512, dt == LAK_F64 ? 4 : 8, dt == LAK_F64 ? 32 : 16, LAK_INC_GLOBAL};
-    case LAK_OP_GEMV_ROW: return {128, 0, dt == LAK_F64 ? 16 : 32, LAK_INC_GLOBAL};
-    case LAK_OP_GEMV_COL: return {512, 0, 32, LAK_INC_LOCAL};
-    case LAK_OP_SPMV: return {64, 0, 0, LAK_INC_GLOBAL};
-    default: return {256, 0, 16, LAK_INC_GLOBAL};
+    case LAK_OP_DOT: return 2 * n * es;
+    case LAK_OP_AXPY: return 3 * n * es;
+    case LAK_OP_GEMV_ROW:
+    case LAK_OP_GEMV_COL: return (m * n + m + n) * es;
+    case LAK_OP_SPMV: return nnz * (es + 4) + (m + 1) * 4 + (m + n) * es;
+    default: return 0;
+    }
+}
+
+int bucket_of(int64_t bytes) {
+    int b = 0;
+    while (b < LAK_SIZE_BUCKETS - 1 && bytes >= kBucketBound[b]) ++b;
+    return b;
+}
+
+// Built-in defaults per op, storage type and size bucket, measured on GB300
+// with the autotuner (every combination of block 64..512, grid 1..32 blocks
+// per SM or automatic, vec 1..16 and both increments, at the sweep sizes that
+// fall in each bucket; the entry kept has the best worst-case ratio to each
+// size's own optimum).  Like the paper's GPU guideline (Sec. 4) the entries
+// for large calls favour many work-groups and the global increment; unlike
+// it, wide per-thread accesses pay off there (32-64 bytes per thread per
+// step), while calls of a few MB prefer narrow accesses and fewer blocks.
+//   block        threads per block
+//   grid_per_sm  vector ops: cap of the automatic grid, in blocks per SM;
+//                dense_gemv / csr_spmv: the grid itself in blocks per SM
+//                (0 = the op's automatic grid)
+//   vec          elements per access for the row's type (FP32 row: BF16/FP16
+//                take the same bytes per access; csr_spmv: loads per lane)
+//   inc          LAK_INC_GLOBAL / LAK_INC_LOCAL
+struct DefaultCfg {
+    int block, grid_per_sm, vec, inc;
+};
+
+constexpr int G_ = LAK_INC_GLOBAL, L_ = LAK_INC_LOCAL;
+// [op][0 = FP32 (and BF16/FP16), 1 = FP64][bucket]
+constexpr DefaultCfg kDefaults[LAK_OP_COUNT][2][LAK_SIZE_BUCKETS] = {
+    // copy
+    {{{128, 32, 8, G_}, {128, 8, 16, L_}, {256, 32, 8, G_}, {512, 32, 16, G_}},
+     {{512, 4, 4, G_}, {64, 32, 8, G_}, {256, 32, 4, G_}, {512, 32, 8, G_}}},
+    // axpy (and axpby, the fused update + norm)
+    {{{256, 32, 8, G_}, {128, 32, 4, G_}, {128, 32, 8, G_}, {512, 32, 16, G_}},
+     {{256, 16, 2, G_}, {256, 16, 2, G_}, {128, 32, 4, G_}, {512, 32, 8, G_}}},
+    // dot
+    {{{256, 8, 8, G_}, {512, 4, 4, G_}, {512, 1, 16, G_}, {512, 2, 8, G_}},
+     {{256, 1, 2, G_}, {512, 1, 1, G_}, {512, 2, 1, G_}, {256, 4, 4, G_}}},
+    // row-major GEMV
+    {{{128, 16, 2, L_}, {512, 4, 8, L_}, {128, 8, 8, G_}, {64, 0, 8, G_}},
+     {{128, 8, 4, G_}, {64, 0, 2, G_}, {64, 16, 2, G_}, {64, 0, 4, G_}}},
+    // column-major GEMV
+    {{{512, 0, 4, L_}, {512, 32, 16, G_}, {512, 2, 8, G_}, {128, 0, 4, G_}},
+     {{512, 4, 2, G_}, {512, 4, 2, G_}, {128, 8, 2, L_}, {256, 0, 2, G_}}},
+    // CSR SpMV
+    {{{64, 32, 8, G_}, {64, 16, 8, G_}, {128, 32, 4, G_}, {128, 32, 4, G_}},
+     {{128, 0, 4, G_}, {64, 32, 4, G_}, {64, 0, 8, G_}, {64, 0, 8, G_}}},
+};
+
+bool is_vector_op(lak_op op) { return op == LAK_OP_COPY || op == LAK_OP_AXPY || op == LAK_OP_DOT; }
+
+DefaultCfg default_row(lak_op op, lak_dtype dt, int bucket) {
+    DefaultCfg d = kDefaults[op][dt == LAK_F64 ? 1 : 0][bucket];
+    if ((dt == LAK_BF16 || dt == LAK_F16) && op != LAK_OP_SPMV)
+        d.vec = d.vec * 2 > 16 ? 16 : d.vec * 2;      // same bytes per access as FP32
+    return d;
+}
+
+// The batched persistent kernels (lak_batch_run) were tuned on their own, at
+// ~256 KB work units: they keep these launch shapes.
+struct BatchCfg {
+    int block, bytes, inc;
+};
+
+BatchCfg batch_row(lak_op op, lak_dtype dt) {
+    const bool f64 = dt == LAK_F64;
+    switch (op) {
+    case LAK_OP_AXPY: return {512, 64, LAK_INC_GLOBAL};
+    case LAK_OP_DOT: return {512, f64 ? 32 : 16, LAK_INC_GLOBAL};
+    case LAK_OP_GEMV_ROW: return {128, f64 ? 16 : 32, LAK_INC_GLOBAL};
+    default: return {64, 16, LAK_INC_GLOBAL};      // CSR: 4 loads per lane (see batch_config)
     }
 }
 
@@ -107,21 +177,27 @@ int vec_for_bytes(int bytes, int es) {
     return v;
 }
 
-lak_cfg builtin_default(lak_op op, lak_dtype dt) {
-    const DefaultCfg d = default_row(op, dt);
-    lak_cfg c{d.block, 0, 0, d.inc};
-    c.vec = op == LAK_OP_SPMV ? 4 : vec_for_bytes(d.bytes, esize(dt));
+// The built-in default as a cfg: dense_gemv / csr_spmv entries with a grid
+// carry it (blocks per SM x SMs); the vector ops keep grid 0 (automatic,
+// capped by default_grid_per_sm).
+lak_cfg builtin_default(lak_op op, lak_dtype dt, int bucket) {
+    const DefaultCfg d = default_row(op, dt, bucket);
+    lak_cfg c{d.block, 0, d.vec, d.inc};
+    if (!is_vector_op(op) && d.grid_per_sm > 0) {
+        const DeviceInfo *di = device_info();
+        if (di) c.grid = d.grid_per_sm * di->sms;
+    }
     return c;
 }
 
 // Automatic grid cap (blocks per SM) for the grid-stride vector kernels.
-int default_grid_per_sm(lak_op op, lak_dtype dt) {
-    const int g = default_row(op, dt).grid_per_sm;
+int default_grid_per_sm(lak_op op, lak_dtype dt, int bucket) {
+    const int g = default_row(op, dt, bucket).grid_per_sm;
     return g > 0 ? g : 0;
 }
 
-lak_cfg g_override[LAK_OP_COUNT][4];
-bool g_has_override[LAK_OP_COUNT][4];
+lak_cfg g_override[LAK_OP_COUNT][4][LAK_SIZE_BUCKETS];
+bool g_has_override[LAK_OP_COUNT][4][LAK_SIZE_BUCKETS];
 std::mutex g_cfg_mu;
 
 bool valid_dtype(lak_dtype dt) { return dt == LAK_F32 || dt == LAK_F64 || dt == LAK_BF16 || dt == LAK_F16; }
@@ -143,11 +219,11 @@ lak_status check_cfg(const lak_cfg *c, const char *who) {
 
 // Explicit cfg, else the override table, else the built-in default; zero
 // grid / vec fields stay zero here (filled per op below).
-lak_cfg base_cfg(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
+lak_cfg base_cfg(lak_op op, lak_dtype dt, int bucket, const lak_cfg *cfg) {
     if (cfg && cfg->block != 0) return *cfg;
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    if (g_has_override[op][dt]) return g_override[op][dt];
-    return builtin_default(op, dt);
+    if (g_has_override[op][dt][bucket]) return g_override[op][dt][bucket];
+    return builtin_default(op, dt, bucket);
 }
 
 int pow2_floor(int64_t v) {
@@ -174,16 +250,17 @@ lak_status plan_vector(lak_op op, lak_dtype dt, int64_t n, const lak_cfg *cfg,
                        const void *const *ptrs, int nptrs, VecPlan *out) {
     const DeviceInfo *di = device_info();
     if (!di) return LAK_ECUDA;
-    lak_cfg c = base_cfg(op, dt, cfg);
+    const int bucket = bucket_of(op_bytes(op, dt, n, n, 0));
+    lak_cfg c = base_cfg(op, dt, bucket, cfg);
     const int es = esize(dt);
-    int want = c.vec ? c.vec : builtin_default(op, dt).vec;
+    int want = c.vec ? c.vec : builtin_default(op, dt, bucket).vec;
     int64_t head = 0;
     int vec = ptrs ? pick_vec(want, es, ptrs, nptrs, n, &head) : want;
     const int64_t nchunks = vec > 0 ? (n - head) / vec : n;
     int64_t grid = c.grid;
     if (grid == 0) {
         const int64_t need = ceil_div(nchunks > 0 ? nchunks : 1, c.block);
-        const int per_sm = default_grid_per_sm(op, dt);
+        const int per_sm = default_grid_per_sm(op, dt, bucket);
         const int64_t cap = per_sm > 0 ? (int64_t)per_sm * di->sms : waves_grid(di, c.block);
         grid = need < cap ? need : cap;
     }
@@ -205,9 +282,10 @@ lak_status plan_gemv_row(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const 
                          const void *A, const void *x, RowPlan *out) {
     const DeviceInfo *di = device_info();
     if (!di) return LAK_ECUDA;
-    lak_cfg c = base_cfg(LAK_OP_GEMV_ROW, dt, cfg);
+    const int bucket = bucket_of(op_bytes(LAK_OP_GEMV_ROW, dt, m, n, 0));
+    lak_cfg c = base_cfg(LAK_OP_GEMV_ROW, dt, bucket, cfg);
     const int es = esize(dt);
-    const int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_ROW, dt).vec;
+    const int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_ROW, dt, bucket).vec;
     (void)A;   // rows are brought to the access width in the kernel (per-row head)
     (void)x;
     (void)lda;
@@ -238,9 +316,10 @@ lak_status plan_gemv_col(lak_dtype dt, int64_t m, int64_t n, int64_t lda, const 
                          const void *A, ColPlan *out) {
     const DeviceInfo *di = device_info();
     if (!di) return LAK_ECUDA;
-    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dt, cfg);
+    const int bucket = bucket_of(op_bytes(LAK_OP_GEMV_COL, dt, m, n, 0));
+    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dt, bucket, cfg);
     const int es = esize(dt);
-    int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dt).vec;
+    int vec = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dt, bucket).vec;
     while (vec > 1) {
         const int w = access_bytes(vec, es);
         if ((!A || (uintptr_t)A % w == 0) && ((lda * es) % w == 0)) break;
@@ -294,11 +373,13 @@ int64_t spmv_seg_max_mean() {
     return v;
 }
 
-lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, SpmvPlan *out) {
+lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t n, int64_t nnz, const lak_cfg *cfg,
+                     SpmvPlan *out) {
     const DeviceInfo *di = device_info();
     if (!di) return LAK_ECUDA;
-    lak_cfg c = base_cfg(LAK_OP_SPMV, dt, cfg);
-    int vec = c.vec ? c.vec : builtin_default(LAK_OP_SPMV, dt).vec;
+    const int bucket = bucket_of(op_bytes(LAK_OP_SPMV, dt, m, n, nnz));
+    lak_cfg c = base_cfg(LAK_OP_SPMV, dt, bucket, cfg);
+    int vec = c.vec ? c.vec : builtin_default(LAK_OP_SPMV, dt, bucket).vec;
     const int64_t mean = m > 0 ? ceil_div(nnz, m) : 1;
     int G = 0;
     int64_t rows_per_block;
@@ -323,9 +404,10 @@ lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t nnz, const lak_cfg *cfg, S
 
 }  // namespace
 
-lak_cfg base_config(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
-    lak_cfg c = base_cfg(op, dt, cfg);
-    if (c.vec == 0) c.vec = builtin_default(op, dt).vec;
+lak_cfg batch_config(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
+    const BatchCfg b = batch_row(op, dt);
+    lak_cfg c = (cfg && cfg->block != 0) ? *cfg : lak_cfg{b.block, 0, 0, b.inc};
+    if (c.vec == 0) c.vec = op == LAK_OP_SPMV ? 4 : vec_for_bytes(b.bytes, esize(dt));
     return c;
 }
 
@@ -371,21 +453,35 @@ LAK_API const char *lak_last_error(void) { return g_msg; }
 
 LAK_API int32_t lak_abi_version(void) { return 1; }
 
-LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg) {
-    if (!valid_op(op)) return fail(LAK_EINVAL, "lak_set_default_cfg: unknown op %d", (int)op);
-    if (!valid_dtype(dtype)) return fail(LAK_EDTYPE, "lak_set_default_cfg: unknown dtype %d", (int)dtype);
+LAK_API lak_status lak_set_default_cfg_bucket(lak_op op, lak_dtype dtype, int32_t bucket,
+                                              const lak_cfg *cfg) {
+    const char *who = "lak_set_default_cfg";
+    if (!valid_op(op)) return fail(LAK_EINVAL, "%s: unknown op %d", who, (int)op);
+    if (!valid_dtype(dtype)) return fail(LAK_EDTYPE, "%s: unknown dtype %d", who, (int)dtype);
+    if (bucket < -1 || bucket >= LAK_SIZE_BUCKETS)
+        return fail(LAK_EINVAL, "%s: bucket %d not in [-1, %d)", who, (int)bucket, LAK_SIZE_BUCKETS);
     if (cfg && cfg->block == 0)
-        return fail(LAK_EINVAL, "lak_set_default_cfg: cfg.block must be set (or pass NULL)");
-    lak_status st = check_cfg(cfg, "lak_set_default_cfg");
+        return fail(LAK_EINVAL, "%s: cfg.block must be set (or pass NULL)", who);
+    lak_status st = check_cfg(cfg, who);
     if (st != LAK_OK) return st;
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    if (cfg) {
-        g_override[op][dtype] = *cfg;
-        g_has_override[op][dtype] = true;
-    } else {
-        g_has_override[op][dtype] = false;
+    for (int b = 0; b < LAK_SIZE_BUCKETS; ++b) {
+        if (bucket >= 0 && b != bucket) continue;
+        if (cfg) g_override[op][dtype][b] = *cfg;
+        g_has_override[op][dtype][b] = cfg != nullptr;
     }
     return LAK_OK;
+}
+
+LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg) {
+    return lak_set_default_cfg_bucket(op, dtype, -1, cfg);
+}
+
+LAK_API int32_t lak_size_bucket(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz) {
+    if (!valid_op(op)) return fail(LAK_EINVAL, "lak_size_bucket: unknown op %d", (int)op);
+    if (!valid_dtype(dtype)) return fail(LAK_EDTYPE, "lak_size_bucket: unknown dtype %d", (int)dtype);
+    if (m < 0 || n < 0 || nnz < 0) return fail(LAK_EINVAL, "lak_size_bucket: negative size");
+    return bucket_of(op_bytes(op, dtype, m, n, nnz));
 }
 
 LAK_API lak_status lak_resolve_cfg(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz,
@@ -419,7 +515,7 @@ LAK_API lak_status lak_resolve_cfg(lak_op op, lak_dtype dtype, int64_t m, int64_
     }
     case LAK_OP_SPMV: {
         SpmvPlan p;
-        st = plan_spmv(dtype, m, nnz, cfg, &p);
+        st = plan_spmv(dtype, m, n, nnz, cfg, &p);
         L = p.L;
         break;
     }
@@ -472,7 +568,7 @@ LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg)
     // per thread would need more blocks only without the cap): size for the
     // widest grid any alignment of these n elements can produce.
     VecPlan p1;
-    lak_cfg c = base_cfg(LAK_OP_DOT, dtype, cfg);
+    lak_cfg c = base_cfg(LAK_OP_DOT, dtype, bucket_of(op_bytes(LAK_OP_DOT, dtype, n, n, 0)), cfg);
     c.vec = 1;
     if (plan_vector(LAK_OP_DOT, dtype, n, &c, nullptr, 0, &p1) != LAK_OK) return 0;
     const int grid = p1.L.grid > p.L.grid ? p1.L.grid : p.L.grid;
@@ -551,8 +647,9 @@ LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout, lak
     // the widest vec the call could pick gives the fewest tiles; narrower vecs
     // (forced by alignment) only add tiles, so size for vec = 1 as well
     size_t best = 0;
-    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dtype, cfg);
-    const int want = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dtype).vec;
+    const int bucket = bucket_of(op_bytes(LAK_OP_GEMV_COL, dtype, m, n, 0));
+    lak_cfg c = base_cfg(LAK_OP_GEMV_COL, dtype, bucket, cfg);
+    const int want = c.vec ? c.vec : builtin_default(LAK_OP_GEMV_COL, dtype, bucket).vec;
     for (int v = want; v >= 1; v >>= 1) {
         lak_cfg cv = c;
         cv.vec = v;
@@ -640,7 +737,7 @@ LAK_API size_t vec_axpy_norm2_workspace(int64_t n, lak_dtype dtype, const lak_cf
         return 0;
     VecPlan p, p1;
     if (plan_vector(LAK_OP_AXPY, dtype, n, cfg, nullptr, 0, &p) != LAK_OK) return 0;
-    lak_cfg c = base_cfg(LAK_OP_AXPY, dtype, cfg);
+    lak_cfg c = base_cfg(LAK_OP_AXPY, dtype, bucket_of(op_bytes(LAK_OP_AXPY, dtype, n, n, 0)), cfg);
     c.vec = 1;
     if (plan_vector(LAK_OP_AXPY, dtype, n, &c, nullptr, 0, &p1) != LAK_OK) return 0;
     const int grid = p1.L.grid > p.L.grid ? p1.L.grid : p.L.grid;
@@ -734,7 +831,7 @@ LAK_API lak_status csr_spmv(void *y, const int32_t *row_ptr, const int32_t *col_
         !aligned_elem(row_ptr, 4) || !aligned_elem(col_idx, 4))
         return fail(LAK_EINVAL, "csr_spmv: pointers not aligned to their element size");
     SpmvPlan p;
-    st = plan_spmv(dtype, m, nnz, cfg, &p);
+    st = plan_spmv(dtype, m, n, nnz, cfg, &p);
     if (st != LAK_OK) return st;
     return launch_spmv(dtype, y, row_ptr, col_idx, vals, x, m, p.L, p.group, (cudaStream_t)stream);
 }

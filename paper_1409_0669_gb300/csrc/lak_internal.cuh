@@ -61,9 +61,10 @@ inline int access_bytes(int vec, int es) {
     return b > 32 ? 32 : b;
 }
 
-// The configuration a call would start from (explicit cfg, else the default
-// table), with vec filled in; host only, no CUDA call; grid left as given.
-lak_cfg base_config(lak_op op, lak_dtype dt, const lak_cfg *cfg);
+// The configuration a batched launch starts from (explicit cfg, else the
+// batched kernels' own defaults), with vec filled in; host only, no CUDA
+// call; grid left as given.
+lak_cfg batch_config(lak_op op, lak_dtype dt, const lak_cfg *cfg);
 
 // Largest vec <= want (power of two) whose access width divides the byte
 // offsets of every pointer in `ptrs` modulo the access width identically, so

@@ -97,6 +97,57 @@ def test_host_side_argument_checks(lib):
     assert lib.lak_set_default_cfg(0, 0, None) == LAK_OK
 
 
+def test_size_buckets(lib):
+    """Bucket = algorithmic bytes against 8 / 64 / 512 MiB (host only)."""
+    from paper_1409_0669_gb300._native import LAK_EINVAL, LAK_EDTYPE, LakCfg
+    MiB = 1 << 20
+    # copy / dot: 2 n s bytes; axpy 3 n s
+    for op, k in ((0, 2), (2, 2), (1, 3)):
+        for s, dt in ((4, 0), (8, 1), (2, 2)):
+            for bound, b in ((8 * MiB, 1), (64 * MiB, 2), (512 * MiB, 3)):
+                n = -(-bound // (k * s))             # first n at or above the bound
+                assert lib.lak_size_bucket(op, dt, n, n, 0) == b, (op, dt, n)
+                if (n - 1) * k * s < bound:
+                    assert lib.lak_size_bucket(op, dt, n - 1, n - 1, 0) == b - 1
+    assert lib.lak_size_bucket(0, 0, 0, 0, 0) == 0
+    # dense GEMV: (mn + m + n) s
+    assert lib.lak_size_bucket(3, 1, 2048, 2048, 0) == 1       # 33.6 MB
+    assert lib.lak_size_bucket(4, 0, 16384, 16384, 0) == 3     # 1.07 GB
+    assert lib.lak_size_bucket(3, 0, 4096, 4096, 0) == 2       # 67 MB
+    # CSR: nnz (s + 4) + (m + 1) 4 + (m + n) s -- the 3D Laplacian 128^3 in FP32
+    assert lib.lak_size_bucket(5, 0, 128 ** 3, 128 ** 3, 14_581_760) == 2
+    assert lib.lak_size_bucket(5, 0, 256 ** 2, 256 ** 2, 326_656) == 0
+    assert lib.lak_size_bucket(7, 0, 1, 1, 0) == LAK_EINVAL
+    assert lib.lak_size_bucket(0, 9, 1, 1, 0) == LAK_EDTYPE
+    assert lib.lak_size_bucket(0, 0, -1, 1, 0) == LAK_EINVAL
+    # per-bucket defaults: bucket range is -1 (all) .. 3
+    cfg = ctypes.byref(LakCfg(128, 0, 4, 0))
+    assert lib.lak_set_default_cfg_bucket(0, 0, 4, cfg) == LAK_EINVAL
+    assert lib.lak_set_default_cfg_bucket(0, 0, -2, cfg) == LAK_EINVAL
+    for b in (-1, 0, 3):
+        assert lib.lak_set_default_cfg_bucket(0, 0, b, cfg) == 0
+    assert lib.lak_set_default_cfg_bucket(0, 0, -1, None) == 0
+
+
+def test_bucket_choice_keeps_best_worst_case():
+    """autotune.choose_per_bucket: per bucket, the config with the best worst
+    ratio over that bucket's sizes (host logic, made-up timings)."""
+    from paper_1409_0669_gb300.autotune import choose_per_bucket
+    res = {
+        100: [{"cfg": [64, 0, 1, 0], "us": 5.0}, {"cfg": [128, 0, 2, 0], "us": 5.5},
+              {"cfg": [256, 0, 4, 0], "us": 9.0}],
+        200: [{"cfg": [64, 0, 1, 0], "us": 12.0}, {"cfg": [128, 0, 2, 0], "us": 8.5},
+              {"cfg": [256, 0, 4, 0], "us": 8.0}],
+        900: [{"cfg": [64, 0, 1, 0], "us": 50.0}, {"cfg": [256, 0, 4, 0], "us": 30.0}],
+    }
+    per = choose_per_bucket(res, {100: 1, 200: 1, 900: 2})
+    # bucket 1: [128,0,2,0] has worst ratio min(5/5.5, 8/8.5) = 0.909; [64..] 0.667; [256..] 0.556
+    assert per[1]["cfg"] == [128, 0, 2, 0]
+    assert abs(per[1]["worst_ratio"] - 5.0 / 5.5) < 1e-12
+    assert per[1]["sizes"] == [100, 200]
+    assert per[2]["cfg"] == [256, 0, 4, 0] and per[2]["worst_ratio"] == 1.0
+
+
 def test_python_binding_imports_and_fails_loudly_without_library(tmp_path):
     from paper_1409_0669_gb300 import _native
     with pytest.raises(ImportError, match="no CPU fallback"):

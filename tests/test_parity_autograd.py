@@ -126,3 +126,32 @@ def test_differentiation_workload_sizes():
     ag.dot(a, b).backward()
     torch.cuda.synchronize()
     assert torch.equal(a.grad, b.detach()) and torch.equal(b.grad, a.detach())
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+@pytest.mark.parametrize("mean_len", [3, 17, 20, 150])
+def test_sampled_outer_lane_groups(storage, mean_len):
+    """Every lane-group width of the sampled outer product (one thread per row
+    for short rows; 8, 16 and 32 lanes for longer ones), ragged row lengths and
+    empty rows, bit-exact against the oracle's one rounded product per entry."""
+    m = 1537
+    rp, ci, _ = synth.random_csr(m, 3001, 40 + mean_len, storage, 0, 2 * mean_len, 0.15, True)
+    dy = synth.uniform(m, 41, storage).cuda()
+    x = synth.uniform(3001, 42, storage).cuda()
+    dv = lak().csr_sampled_outer(rp.cuda(), ci.cuda(), dy, x)
+    torch.cuda.synchronize()
+    ref = oracle.round_to(oracle.sampled_outer(rp, ci, dy.cpu(), x.cpu()), storage)
+    assert np.array_equal(host(dv), ref)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n", [(1, 7), (5000, 33), (700, 4099)])
+def test_dense_outer_row_loop(storage, m, n):
+    """dense_outer with more rows than row groups (each block walks many rows),
+    a column count that is not a multiple of the vector width, and one row."""
+    dy = synth.uniform(m, 43, storage).cuda()
+    x = synth.uniform(n, 44, storage).cuda()
+    dA = lak().dense_outer(dy, x)
+    torch.cuda.synchronize()
+    ref = oracle.round_to(oracle.dense_outer(dy.cpu(), x.cpu()).ravel(), storage)
+    assert np.array_equal(host(dA), ref)

@@ -1,0 +1,95 @@
+"""Per-size-bucket launch defaults on the device: the configuration a call
+resolves to follows its size bucket, per-bucket overrides stay in their
+bucket, the autotuner's bucket cache installs into the right buckets, and a
+bucket tuning pass on two sizes keeps a configuration that was timed."""
+import json
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def lak():
+    import paper_1409_0669_gb300 as m
+    return m
+
+
+def sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def test_resolve_follows_bucket():
+    m = lak()
+    # FP64 dot: 1e6 elements = 16 MB (bucket 1), 1e8 = 1.6 GB (bucket 3)
+    assert m.size_bucket("dot", "f64", 10 ** 6, 10 ** 6) == 1
+    assert m.size_bucket("dot", "f64", 10 ** 8, 10 ** 8) == 3
+    c1 = m.resolve_cfg("dot", "f64", 10 ** 6, 10 ** 6)
+    c3 = m.resolve_cfg("dot", "f64", 10 ** 8, 10 ** 8)
+    assert (c1.block, c1.vec) == (512, 1) and c1.grid == min(sms(), -(-10 ** 6 // 512))
+    assert (c3.block, c3.vec) == (256, 4) and c3.grid == 4 * sms()
+    # column-major FP64 GEMV 2048^2 (33.6 MB, bucket 1): explicit grid from the table
+    g = m.resolve_cfg("gemv_col", "f64", 2048, 2048)
+    assert g.block == 512 and g.vec == 2
+    # BF16 takes the FP32 row's bytes per access: copy bucket 3 = 64 B -> 16 x 2 B... capped at 16
+    b = m.resolve_cfg("copy", "bf16", 10 ** 9, 10 ** 9)
+    assert b.vec == 16
+
+
+def test_bucket_override_stays_in_its_bucket():
+    m = lak()
+    n_small, n_large = 10 ** 5, 10 ** 8
+    b_small = m.size_bucket("axpy", "f32", n_small, n_small)
+    before_large = m.resolve_cfg("axpy", "f32", n_large, n_large)
+    try:
+        m.set_default_cfg("axpy", "f32", (96, 0, 2, 1), bucket=b_small)
+        s = m.resolve_cfg("axpy", "f32", n_small, n_small)
+        assert (s.block, s.vec, s.increment) == (96, 2, 1)
+        l = m.resolve_cfg("axpy", "f32", n_large, n_large)
+        assert (l.block, l.grid, l.vec, l.increment) == (before_large.block, before_large.grid,
+                                                         before_large.vec, before_large.increment)
+        # the call itself runs with the override and is exact
+        y = torch.rand(n_small, device="cuda")
+        z = torch.rand(n_small, device="cuda")
+        x = torch.empty_like(y)
+        m.vec_axpy(x, y, z, 0.5)
+        assert torch.equal(x, torch.addcmul(y, z, torch.tensor(0.5, device="cuda")))
+    finally:
+        m.set_default_cfg("axpy", "f32", None)
+
+
+def test_apply_cache_with_bucket_keys(tmp_path):
+    from paper_1409_0669_gb300 import autotune
+    m = lak()
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({autotune.cache_key(): {"copy:f64:2": [64, 0, 1, 0]}}))
+    try:
+        assert autotune.apply_cache(str(path)) == 1
+        n2 = 10 ** 7                                    # 160 MB: bucket 2
+        assert m.size_bucket("copy", "f64", n2, n2) == 2
+        c = m.resolve_cfg("copy", "f64", n2, n2)
+        assert (c.block, c.vec) == (64, 1)
+        c0 = m.resolve_cfg("copy", "f64", 1000, 1000)
+        assert c0.block != 64 or c0.vec != 1
+    finally:
+        m.set_default_cfg("copy", "f64", None)
+
+
+def test_tune_buckets_small_space():
+    """Two sizes in two buckets, three candidate configs: the kept config of
+    each bucket is one of the candidates and its reported worst ratio is 1 for
+    a single-size bucket."""
+    from paper_1409_0669_gb300 import autotune
+    from paper_1409_0669_gb300._native import LakCfg
+    cands = [LakCfg(128, 0, 4, 0), LakCfg(256, 0, 2, 0), LakCfg(512, 0, 8, 1)]
+    results, buckets = {}, {}
+    for n in (100_000, 3_000_000):
+        prob = autotune.Problem("axpy", "f32", n)
+        results[n] = autotune.tune("axpy", "f32", n, reps=5, cfgs=cands, problem=prob)
+        buckets[n] = autotune.problem_bucket(prob)
+        assert all(r["us"] >= 0 for r in results[n])
+    assert buckets[100_000] == 0 and buckets[3_000_000] == 1
+    per = autotune.choose_per_bucket(results, buckets)
+    for b in (0, 1):
+        assert per[b]["cfg"] in [list(c.as_tuple()) for c in cands]
+        assert per[b]["worst_ratio"] == 1.0
