@@ -70,6 +70,7 @@ def _bind(path: str):
         "orc_axpy": (None, [_F64P, _F64P, _F64P, ctypes.c_double, _I64]),
         "orc_axpby": (None, [_F64P, ctypes.c_double, _F64P, ctypes.c_double, _F64P, _I64]),
         "orc_dot": (ctypes.c_double, [_F64P, _F64P, _I64, _F64P]),
+        "orc_sparse_dot": (ctypes.c_double, [_F64P, _I32P, _F64P, _I64]),
         "orc_scale": (None, [_F64P, _F64P, ctypes.c_double, _I64]),
         "orc_gemv": (None, [_F64P, _F64P, _F64P, _I64, _I64, _I64, ctypes.c_int]),
         "orc_gemv_entry": (ctypes.c_double, [_F64P, _F64P, _I64, _I64, _I64, ctypes.c_int]),
@@ -182,6 +183,15 @@ def dot(x, y, with_lo: bool = False):
     lo = ctypes.c_double(0.0)
     hi = _load().orc_dot(_ptr(xv, _F64P), _ptr(yv, _F64P), xv.size, ctypes.byref(lo))
     return (hi, lo.value) if with_lo else hi
+
+
+def sparse_dot(vals, idx, y) -> float:
+    """sum_k vals[k] * y[idx[k]] (compensated, increasing k)."""
+    vv, yv, iv = widen(vals), widen(y), _i32(idx)
+    assert vv.size == iv.size
+    if iv.size:
+        assert 0 <= int(iv.min()) and int(iv.max()) < yv.size
+    return _load().orc_sparse_dot(_ptr(vv, _F64P), _ptr(iv, _I32P), _ptr(yv, _F64P), vv.size)
 
 
 def scale(v, s: float) -> np.ndarray:

@@ -112,6 +112,20 @@ double orc_dot(const double *x, const double *y, int64_t n, double *lo)
     return acc_value(&acc, lo);
 }
 
+/*
+ * Inner product of a sparse vector with a dense one: s = sum_k v_k y_{c_k},
+ * where the sparse vector holds nnz stored values v_k at positions c_k
+ * (paper Sec. 2's inner product with one operand given by its nonzeros; each
+ * row of a CSR product y = A x is one such sum).  Compensated sum in
+ * increasing k, as in orc_dot.
+ */
+double orc_sparse_dot(const double *v, const int32_t *c, const double *y, int64_t nnz)
+{
+    orc_acc acc = {0.0, 0.0};
+    for (int64_t k = 0; k < nnz; ++k) acc_add_prod(&acc, v[k], y[c[k]]);
+    return acc_value(&acc, NULL);
+}
+
 /* Scaling out <- s * v (the backward of the inner product: d<x,y>/dx = y). */
 void orc_scale(double *out, const double *v, double s, int64_t n)
 {

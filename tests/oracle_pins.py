@@ -145,6 +145,43 @@ def pin_dot_fraction_random():
         assert abs(Fraction(hi) + Fraction(lo) - exact) <= abs(exact) * Fraction(2) ** -100
 
 
+def pin_sparse_dot_fraction_and_closed_forms():
+    """Sparse inner product: exact rational brute force (correctly rounded
+    result), repeated indices, the ones/arange closed form, and the empty sum."""
+    g = synth.rng(15)
+    for nnz, n in ((1, 3), (7, 5), (64, 1000), (300, 40)):
+        v = g.standard_normal(nnz) * 10.0 ** g.integers(-4, 4, nnz)
+        y = g.standard_normal(n) * 10.0 ** g.integers(-4, 4, n)
+        c = g.integers(0, n, nnz).astype(np.int32)        # repeats allowed
+        exact = sum(Fraction(v[k]) * Fraction(y[c[k]]) for k in range(nnz))
+        assert oracle.sparse_dot(v, c, y) == _frac_round(exact)
+    # ones against arange: sum of the indices themselves
+    c = np.array([5, 0, 5, 3, 9, 9, 9], dtype=np.int32)
+    assert oracle.sparse_dot(np.ones(7), c, np.arange(10.0)) == 40.0
+    # first and last stored entries both count
+    assert oracle.sparse_dot(np.array([2.0, 0.0, 3.0]), np.array([1, 0, 2], np.int32),
+                             np.array([0.0, 7.0, 11.0])) == 47.0
+    assert oracle.sparse_dot(np.zeros(0), np.zeros(0, np.int32), np.ones(4)) == 0.0
+
+
+def pin_sparse_dot_is_a_csr_row():
+    """Each entry of a CSR product (brute-force dense product) is the sparse
+    inner product of that row's stored entries with x."""
+    rp, ci, v = synth.random_csr(40, 25, 16, "f64", 0, 9, 0.1, True)
+    rp, ci, v = rp.numpy(), ci.numpy(), v.numpy()
+    x = synth.uniform(25, 17, "f64").numpy()
+    dense = np.zeros((40, 25))
+    for i in range(40):
+        for k in range(rp[i], rp[i + 1]):
+            dense[i, ci[k]] += v[k]
+    for i in range(40):
+        a, b = rp[i], rp[i + 1]
+        exact = sum(Fraction(dense[i, j]) * Fraction(x[j]) for j in range(25)) \
+            if len(set(ci[a:b])) == b - a else \
+            sum(Fraction(v[k]) * Fraction(x[ci[k]]) for k in range(a, b))
+        assert oracle.sparse_dot(v[a:b], ci[a:b], x) == _frac_round(exact)
+
+
 # ---- dense matrix-vector product (Sec. 2) -----------------------------------------
 
 def pin_gemv_identity_and_single_entry():
@@ -504,6 +541,7 @@ PINS = [
     pin_axpy_exact_rational, pin_axpby_exact_rational,
     pin_dot_ones, pin_dot_arange_closed_forms, pin_dot_alternating_and_unit, pin_dot_fsum_f32,
     pin_dot_cancellation, pin_dot_fraction_random,
+    pin_sparse_dot_fraction_and_closed_forms, pin_sparse_dot_is_a_csr_row,
     pin_gemv_identity_and_single_entry, pin_gemv_exact_tiny, pin_gemv_numpy,
     pin_gemv_linearity_and_entries,
     pin_spmv_golden, pin_spmv_laplacian_ones, pin_spmv_eigen_2d, pin_spmv_eigen_3d,

@@ -25,6 +25,10 @@ MUTANTS = [
     ("axpby_drop_scale", "double ay = alpha_y * y[i];", "double ay = y[i];"),
     ("dot_drop_first_term", "for (int64_t i = 0; i < n; ++i) acc_add_prod(&acc, x[i], y[i]);",
      "for (int64_t i = 1; i < n; ++i) acc_add_prod(&acc, x[i], y[i]);"),
+    ("sparse_dot_gather_by_position", "acc_add_prod(&acc, v[k], y[c[k]]);",
+     "acc_add_prod(&acc, v[k], y[k < nnz ? c[0] : 0]);"),
+    ("sparse_dot_drop_last", "for (int64_t k = 0; k < nnz; ++k) acc_add_prod(&acc, v[k], y[c[k]]);",
+     "for (int64_t k = 0; k + 1 < nnz; ++k) acc_add_prod(&acc, v[k], y[c[k]]);"),
     ("gemv_row_transposed",
      "double a = (layout == 0) ? A[i * lda + j] : A[i + j * lda];\n            acc_add_prod(&acc, a, x[j]);\n        }\n        y[i]",
      "double a = (layout == 0) ? A[j * lda + i] : A[i + j * lda];\n            acc_add_prod(&acc, a, x[j]);\n        }\n        y[i]"),
