@@ -1084,6 +1084,22 @@ def run_gb300(args):
         summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
                         "us": round(t * 1e3, 2), "bound": b["bound"],
                         "frac_bound": round(b["frac"], 4)}
+    # CSR SpMV: the floor set by its x gather -- the sparse inner product over
+    # the matrix's own entries (vec_dot_sparse) timed alone
+    with torch.cuda.stream(stream):
+        floors = gather_floors(per, lak)
+    # The sparse inner product is a floor only where the columns are random (the
+    # power-law matrix): a stencil's x reuse lets a row-parallel kernel beat an
+    # entry-parallel gather, so there it is reported but the roof stays HBM.
+    for key, (g_us, name) in floors.items():
+        if key in summary:
+            t_us = summary[key]["us"]
+            hbm_us = per[name][0].nbytes / (peak * 1e9) * 1e6
+            summary[key]["gather_floor_us"] = round(g_us, 2)
+            summary[key]["frac_gather_floor"] = round(g_us / t_us, 4)
+            if "powerlaw" in name and g_us > hbm_us:
+                summary[key]["bound"] = "gather"
+                summary[key]["frac_bound"] = round(g_us / t_us, 4)
     for name in ("copy_f64_2154435", "axpy_f64_2154435", "dot_f64_2154435",
                  "gemv_row_f64_2048"):
         if name in per:
@@ -1119,6 +1135,12 @@ def run_gb300(args):
     formats = None
     if not args.no_formats and not args.only and rank == 0:
         formats = run_formats(device)
+    small = None
+    if not args.no_small and not args.only and rank == 0:
+        small = run_small(device)
+    curves = None
+    if not args.no_curves and not args.only and rank == 0:
+        curves = run_size_curves(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1131,8 +1153,9 @@ def run_gb300(args):
         "config": {"workload": WORKLOAD if not args.only else f"subset /{args.only}/ of: "
                    + WORKLOAD, "bytes_per_step": bytes_per_step,
                    "launches_per_step": len(items),
-                   "l2": "inputs larger than L2: each buffer read once per step, >1 GB of other "
-                         "traffic between reuses (no explicit flush)",
+                   "l2": "cold at every launch without an explicit flush: launches are "
+                         "ordered so that more than 1 GB (8x L2) of other traffic passes "
+                         "between two uses of any buffer",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline, "per_kernel": summary, "e2e": e2e,
         "gpu_launches": len(items) * K, "clocks": clocks,
@@ -1149,12 +1172,136 @@ def run_gb300(args):
         line["fused"] = fused
     if formats is not None:
         line["spmv_formats"] = formats
+    if small is not None:
+        line["small_config"] = small
+    if curves is not None:
+        line["size_curves"] = curves
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     del keep
     return 0
+
+
+def gather_floors(per, lak, reps=20):
+    """For every timed CSR SpMV launch: the device time of the sparse inner
+    product sum_k vals[k] x[col_idx[k]] over the matrix's own values and
+    column indices (vec_dot_sparse) -- every stored entry streamed and its x
+    gathered exactly as a CSR product must, without the rows.  No CSR kernel
+    on that matrix can be faster where the gather, not HBM, is the limit.
+    Returns {summary key: (us, launch name)}."""
+    import torch
+    from paper_1409_0669_gb300.timing import launch_time_us
+    out = {}
+    for name, (it, _) in per.items():
+        if it.op != "spmv":
+            continue
+        cid, vd, xsp = it.h2d[1], it.h2d[2], it.h2d[3]
+        o = torch.empty(1, dtype=torch.float64 if it.dtype == "f64" else torch.float32,
+                        device=xsp.device)
+        ws = torch.zeros(lak.vec_dot_sparse_workspace(cid.numel(), it.dtype), dtype=torch.uint8,
+                         device=xsp.device)
+        lak.vec_dot_sparse(vd, cid, xsp, out=o, workspace=ws)
+        us = launch_time_us(lambda: lak.vec_dot_sparse(vd, cid, xsp, out=o, workspace=ws), reps)
+        out[f"spmv_{name.split('_')[1]}_{it.dtype}"] = (us, name)
+        del ws
+    return out
+
+
+def run_small(device, reps=200):
+    """The small FP32 configuration: 2D 5-point Laplacian 256^2 (65,536 rows,
+    values 4/-1), x = y + 0.5 z and <x, y> on n = 65,536 (U(-1,1), seed 0),
+    y = A x in CSR, and a 1024^2 row-major GEMV (N(0,1)).  Latency bound, so
+    reported in microseconds: each call issued from the host back to back,
+    the four calls in sequence issued from the host, and the same sequence
+    captured once in a CUDA graph and replayed (operands L2-resident)."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    import synth
+    from paper_1409_0669_gb300.timing import warm_time_us
+    dev = device
+    n = 65536
+    y = synth.uniform(n, 0, "f32").to(dev)
+    z = synth.uniform(n, 1, "f32").to(dev)
+    x = torch.empty_like(y)
+    out = torch.zeros(1, device=dev)
+    ws = torch.zeros(max(lak.vec_dot_workspace(n, "f32"), 256), dtype=torch.uint8, device=dev)
+    rp, ci, v = synth.laplacian_2d(256, "f32")
+    rp, ci, v = rp.to(dev), ci.to(dev), v.to(dev)
+    xs = synth.uniform(n, 2, "f32").to(dev)
+    ys = torch.empty(n, device=dev)
+    g = 1024
+    A = synth.device_normal_(torch.empty(g, g, device=dev), 3)
+    xg = synth.uniform(g, 4, "f32").to(dev)
+    yg = torch.empty(g, device=dev)
+    calls = {
+        "axpy": (lambda: lak.vec_axpy(x, y, z, 0.5), 3 * n * 4),
+        "dot": (lambda: lak.vec_dot(x, y, out=out, workspace=ws), 2 * n * 4),
+        "spmv_lap2d_256": (lambda: lak.csr_spmv(rp, ci, v, xs, y=ys),
+                           v.numel() * 8 + rp.numel() * 4 + 2 * n * 4),
+        "gemv_row_1024": (lambda: lak.dense_gemv(A, xg, y=yg), (g * g + 2 * g) * 4),
+    }
+    rep = {}
+    for name, (fn, nbytes) in calls.items():
+        us = warm_time_us(fn, reps)
+        rep[name] = {"us_launches": round(us, 2), "bytes": nbytes,
+                     "GBs": round(nbytes / (us * 1e-6) / 1e9, 1)}
+
+    def sequence():
+        for fn, _ in calls.values():
+            fn()
+    seq_us = warm_time_us(sequence, reps)
+    sequence()
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(gr, stream=cap):
+            sequence()
+    torch.cuda.synchronize()
+    graph_us = warm_time_us(gr.replay, reps)
+    rep["sequence_4_calls"] = {"us_launches": round(seq_us, 2), "us_graph_replay": round(graph_us, 2)}
+    rep["timing"] = ("device time per call, calls back to back in one CUDA-event interval "
+                     "(operands L2-resident); the graph holds the same four calls")
+    return rep
+
+
+def run_size_curves(device, reps=10):
+    """GB/s against size for copy, x = y + 0.5 z and <y, z> (n = 1e3..1e8, 3 per
+    decade) and both GEMV layouts (512^2..16384^2), FP32 and FP64, with the
+    default launch configuration: cold = L2 evicted before every launch (a
+    256 MB read; differential event timing) where the operands fit twice in L2,
+    else launch by launch; warm = operands left in L2 by the previous launch
+    (back-to-back launches), for working sets that fit in L2 only."""
+    import torch
+
+    import synth
+    from paper_1409_0669_gb300 import autotune
+    l2 = torch.cuda.get_device_properties(device).L2_cache_size
+    rows = []
+    for storage in ("f32", "f64"):
+        for op in ("copy", "axpy", "dot"):
+            for n in synth.vector_sweep_sizes():
+                rows.append((op, storage, n))
+        for op in ("gemv_row", "gemv_col"):
+            for n in synth.gemv_sweep_sizes():
+                rows.append((op, storage, n))
+    out = {}
+    for op, storage, n in rows:
+        prob = autotune.Problem(op, storage, n, device)
+        cold = prob.time_cfg(None, reps)
+        rec = {"bytes": prob.nbytes, "cold_us": round(cold, 3),
+               "cold_GBs": round(prob.nbytes / (max(cold, 1e-3) * 1e-6) / 1e9, 1)}
+        if prob.footprint < l2:
+            warm = prob.time_warm(None, 4 * reps)
+            rec.update({"warm_us": round(warm, 3),
+                        "warm_GBs": round(prob.nbytes / (max(warm, 1e-3) * 1e-6) / 1e9, 1)})
+        out.setdefault(f"{op}_{storage}", {})[str(n)] = rec
+        del prob
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(items, keep, stream, device, steps, lib_check, dist):
@@ -1223,6 +1370,10 @@ def main(argv=None):
                     help="skip the fused-vs-separate report")
     ap.add_argument("--no-formats", action="store_true",
                     help="skip the CSR-vs-SELL report")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small-configuration (latency, CUDA graph) report")
+    ap.add_argument("--no-curves", action="store_true",
+                    help="skip the cold/warm GB/s-against-size report")
     ap.add_argument("--profile-set", action="store_true",
                     help="launch every kernel family once at a small footprint (for ncu)")
     ap.add_argument("--only", default=None,

@@ -231,6 +231,24 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
                            const lak_cfg *cfg, void *stream);
 
 /*
+ * vec_dot_sparse: *out = sum_{k<nnz} vals[k] * y[idx[k]] -- the inner product
+ * of Sec. 2 with one operand given by its nonzeros: a sparse vector of nnz
+ * stored values `vals` at positions `idx` (int32) times a dense vector y of n
+ * elements (the sparse BLAS "usdot").  Every row of a CSR product is one such
+ * sum, so its time on a matrix's own (vals, col_idx) is the floor that the
+ * x gather sets for any CSR kernel on that matrix.  Values and indices stream
+ * in packs, y is gathered through L1, and the reduction is vec_dot's (same
+ * configuration, workspace and determinism).  `out` is one device element:
+ * float for F32/BF16/F16, double for F64.  Requirement the library does not
+ * check on the device: 0 <= idx[k] < n; repeated indices are summed.
+ * nnz = 0 writes 0.
+ */
+LAK_API size_t vec_dot_sparse_workspace(int64_t nnz, lak_dtype dtype, const lak_cfg *cfg);
+LAK_API lak_status vec_dot_sparse(void *out, const void *vals, const int32_t *idx, const void *y,
+                                  int64_t nnz, int64_t n, lak_dtype dtype, void *workspace,
+                                  size_t ws_bytes, const lak_cfg *cfg, void *stream);
+
+/*
  * vec_dot_compensated: *out = sum_i x[i] * y[i] for FP32, BF16 or FP16 storage,
  * accumulated with compensated FP32 arithmetic (the inner product of Sec. 2;
  * the scheme is Ogita, Rump and Oishi's Dot2, 2005): each product is split

@@ -24,7 +24,8 @@ from . import _native
 from ._native import DTYPES, INCREMENTS, LAYOUTS, OPS, LakCfg, LakError
 
 __all__ = ["vec_copy", "vec_axpy", "vec_axpby", "vec_axpy_norm2", "vec_axpy_norm2_workspace",
-           "dense_gemv_trans", "vec_dot", "vec_dot_workspace", "vec_dot_compensated",
+           "dense_gemv_trans", "vec_dot", "vec_dot_workspace", "vec_dot_sparse",
+           "vec_dot_sparse_workspace", "vec_dot_compensated",
            "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg",
@@ -247,6 +248,40 @@ def vec_dot(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None
                       _dev_ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                       _cfg_ptr(cfg), sh)
     _native.check("vec_dot", st)
+    return out
+
+
+def vec_dot_sparse_workspace(nnz: int, storage: str, cfg: CfgLike = None) -> int:
+    return int(_lib.vec_dot_sparse_workspace(int(nnz), DTYPES[storage], _cfg_ptr(cfg)))
+
+
+def vec_dot_sparse(vals: torch.Tensor, idx: torch.Tensor, y: torch.Tensor,
+                   out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                   cfg: CfgLike = None, stream=None) -> torch.Tensor:
+    """sum_k vals[k] * y[idx[k]] (idx int32, 0 <= idx < len(y)) into a
+    one-element device tensor (float32 for FP32/BF16/FP16 storage, float64 for
+    FP64)."""
+    s = _same_storage(vals, y)
+    nnz = vals.numel()
+    if idx.numel() != nnz:
+        raise ValueError("vals and idx must have the same length")
+    if idx.dtype != torch.int32:
+        raise TypeError("idx must be int32")
+    odt = torch.float64 if s == "f64" else torch.float32
+    if out is None:
+        out = torch.empty(1, dtype=odt, device=y.device)
+    elif out.dtype != odt or out.numel() < 1:
+        raise TypeError(f"out must be a {odt} tensor with at least one element")
+    sh = _stream(stream)
+    need = vec_dot_sparse_workspace(nnz, s, cfg)
+    if workspace is None:
+        workspace = _workspace(need, sh, y.device)
+    st = _lib.vec_dot_sparse(_dev_ptr(out, "out"), _vec_arg(vals, "vals") if nnz else None,
+                             _vec_arg(idx, "idx") if nnz else None,
+                             _vec_arg(y, "y") if y.numel() else None, nnz, y.numel(), DTYPES[s],
+                             _dev_ptr(workspace, "workspace"),
+                             workspace.numel() * workspace.element_size(), _cfg_ptr(cfg), sh)
+    _native.check("vec_dot_sparse", st)
     return out
 
 

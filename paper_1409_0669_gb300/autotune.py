@@ -44,7 +44,7 @@ import torch
 from . import _native
 from ._native import DTYPES, LakCfg, LakError
 from ._native import OPS as _OP_CODES
-from .timing import launch_time_us
+from .timing import launch_time_us, warm_time_us
 
 OPS = ("copy", "axpy", "dot", "gemv_row", "gemv_col", "spmv")
 BLOCKS = (64, 128, 256, 512)
@@ -164,6 +164,19 @@ class Problem:
                 _native.check(self.op, st)
 
         return launch_time_us(call, reps, self.flush, self.stream)
+
+    def time_warm(self, cfg: Optional[LakCfg], reps: int = 10) -> float:
+        """Device time of one launch with the operands left in L2 by the
+        previous one (back-to-back launches), in microseconds."""
+        import ctypes
+        cptr = ctypes.byref(cfg) if cfg is not None else None
+
+        def call():
+            st = self.fn(cptr)
+            if st != 0:
+                _native.check(self.op, st)
+
+        return warm_time_us(call, reps, self.stream)
 
 
 def tune(op: str, storage: str, size, reps: int = 10, cfgs: Optional[List[LakCfg]] = None,

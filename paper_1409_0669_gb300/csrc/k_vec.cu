@@ -78,9 +78,6 @@ dot_kernel(void *out, const T *__restrict__ x, const T *__restrict__ y, int64_t 
            int64_t head, int64_t nchunks, int inc, unsigned int *counter,
            double *partials) {
     using A = typename Acc<T>::type;
-    __shared__ double wsum[32];
-    __shared__ int am_last;
-
     A acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = A(0);
@@ -109,41 +106,10 @@ dot_kernel(void *out, const T *__restrict__ x, const T *__restrict__ y, int64_t 
 #pragma unroll
         for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
     }
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    A s = group_sum(acc[0], 32);
-    if (lane == 0) wsum[warp] = (double)s;
-    __syncthreads();
-    if (warp == 0) {
-        double b = lane < nwarps ? wsum[lane] : 0.0;
-        b = group_sum(b, 32);
-        if (lane == 0) {
-            partials[blockIdx.x] = b;
-            __threadfence();
-            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
-            am_last = (ticket == gridDim.x - 1);
-        }
-    }
-    __syncthreads();
-    if (!am_last) return;
-
-    __threadfence();
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
-    v = group_sum(v, 32);
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double f = lane < nwarps ? wsum[lane] : 0.0;
-        f = group_sum(f, 32);
-        if (lane == 0) {
-            if constexpr (sizeof(A) == 8)
-                *static_cast<double *>(out) = f;
-            else
-                *static_cast<float *>(out) = __double2float_rn(f);
-        }
-    }
+    if constexpr (sizeof(A) == 8)
+        grid_sum_last_block(acc[0], static_cast<double *>(out), counter, partials);
+    else
+        grid_sum_last_block(acc[0], static_cast<float *>(out), counter, partials);
 }
 
 // ---- compensated dot (FP32 arithmetic on FP32 / BF16 / FP16 storage) --------
@@ -161,8 +127,6 @@ __global__ void __launch_bounds__(512)
 dot_comp_kernel(double *out, const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                 int64_t head, int64_t nchunks, int inc, unsigned int *counter,
                 double *partials) {
-    __shared__ double wsum[32];
-    __shared__ int am_last;
     float sv[V], cv[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) sv[v] = cv[v] = 0.0f;
@@ -198,35 +162,7 @@ dot_comp_kernel(double *out, const T *__restrict__ x, const T *__restrict__ y, i
     double d = 0.0;
 #pragma unroll
     for (int v = 0; v < V; ++v) d += (double)sv[v] + (double)cv[v];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    d = group_sum(d, 32);
-    if (lane == 0) wsum[warp] = d;
-    __syncthreads();
-    if (warp == 0) {
-        double b = lane < nwarps ? wsum[lane] : 0.0;
-        b = group_sum(b, 32);
-        if (lane == 0) {
-            partials[blockIdx.x] = b;
-            __threadfence();
-            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
-            am_last = (ticket == gridDim.x - 1);
-        }
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
-    v = group_sum(v, 32);
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double f = lane < nwarps ? wsum[lane] : 0.0;
-        f = group_sum(f, 32);
-        if (lane == 0) *out = f;
-    }
+    grid_sum_last_block(d, out, counter, partials);
 }
 
 // ---- dispatch ----------------------------------------------------------------

@@ -5,6 +5,9 @@
 //   vec_axpy_norm2     x = y + alpha*z and s = <x, x> in one pass (the update
 //                      and the squared norm of its result, reading y and z once
 //                      and never re-reading x)
+//   vec_dot_sparse     s = sum_k vals[k] * y[idx[k]]: the inner product of a
+//                      sparse vector (stored values and their indices) with a
+//                      dense one -- the gather-bound core of every CSR row
 #include "lak_internal.cuh"
 #include "vec_loop.cuh"
 
@@ -53,8 +56,6 @@ axpy_norm2_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, voi
                   int64_t n, int64_t head, int64_t nchunks, int inc, unsigned int *counter,
                   double *partials) {
     using A = typename Acc<T>::type;
-    __shared__ double wsum[32];
-    __shared__ int am_last;
     A acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = A(0);
@@ -88,40 +89,75 @@ axpy_norm2_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, voi
 #pragma unroll
         for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
     }
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    const A s = group_sum(acc[0], 32);
-    if (lane == 0) wsum[warp] = (double)s;
-    __syncthreads();
-    if (warp == 0) {
-        double b = lane < nwarps ? wsum[lane] : 0.0;
-        b = group_sum(b, 32);
-        if (lane == 0) {
-            partials[blockIdx.x] = b;
-            __threadfence();
-            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
-            am_last = (ticket == gridDim.x - 1);
+    if constexpr (sizeof(A) == 8)
+        grid_sum_last_block(acc[0], static_cast<double *>(out), counter, partials);
+    else
+        grid_sum_last_block(acc[0], static_cast<float *>(out), counter, partials);
+}
+
+// Sparse inner product: the values and indices stream in V-wide packs (the
+// loop skeleton of dot_kernel), each index gathers one element of y through
+// L1, and the sum is finished like dot_kernel's.
+template <typename T, int V>
+__global__ void __launch_bounds__(512)
+dot_sparse_kernel(void *out, const T *__restrict__ vals, const int32_t *__restrict__ idx,
+                  const T *__restrict__ y, int64_t nnz, int64_t head, int64_t nchunks, int inc,
+                  unsigned int *counter, double *partials) {
+    using A = typename Acc<T>::type;
+    A acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = A(0);
+    const Range r = chunk_range(nchunks, inc);
+    for (int64_t c = r.begin; c < r.end; c += r.stride) {
+        const int64_t o = head + c * V;
+        Pack<T, V> pv;
+        Pack<int32_t, V> pi;
+        load_pack<T, V, STREAM>(pv, vals + o);
+        load_pack<int32_t, V, STREAM>(pi, idx + o);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            acc[v] = fma_acc(widen(pv.e[v]), widen(ld_cached(y + pi.e[v])), acc[v]);
+    }
+    {
+        const int64_t body_end = head + nchunks * V;
+        const int64_t nextra = head + (nnz - body_end);
+        const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < nextra) {
+            const int64_t k = extra_index(t, head, body_end);
+            acc[0] = fma_acc(widen(vals[k]), widen(ld_cached(y + idx[k])), acc[0]);
         }
     }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
-    v = group_sum(v, 32);
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double f = lane < nwarps ? wsum[lane] : 0.0;
-        f = group_sum(f, 32);
-        if (lane == 0) {
-            if constexpr (sizeof(A) == 8)
-                *static_cast<double *>(out) = f;
-            else
-                *static_cast<float *>(out) = __double2float_rn(f);
-        }
+#pragma unroll
+    for (int w = 1; w < V; w <<= 1) {
+#pragma unroll
+        for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
     }
+    if constexpr (sizeof(A) == 8)
+        grid_sum_last_block(acc[0], static_cast<double *>(out), counter, partials);
+    else
+        grid_sum_last_block(acc[0], static_cast<float *>(out), counter, partials);
+}
+
+template <typename T>
+lak_status dot_sparse_t(void *out, const void *vals, const int32_t *idx, const void *y,
+                        int64_t nnz, int64_t head, void *ws, const Launch &L, cudaStream_t s) {
+    const T *vp = static_cast<const T *>(vals);
+    const T *yp = static_cast<const T *>(y);
+    unsigned int *counter = static_cast<unsigned int *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
+    const int64_t nchunks = (nnz - head) / L.vec;
+#define LAK_SD(VV)                                                                        \
+    dot_sparse_kernel<T, VV><<<L.grid, L.block, 0, s>>>(out, vp, idx, yp, nnz, head,       \
+                                                        nchunks, L.inc, counter, partials)
+    switch (L.vec) {
+    case 1: LAK_SD(1); break;
+    case 2: LAK_SD(2); break;
+    case 4: LAK_SD(4); break;
+    case 8: LAK_SD(8); break;
+    default: return fail(LAK_EINVAL, "vec_dot_sparse: unsupported vec %d", L.vec);
+    }
+#undef LAK_SD
+    return check_launch("vec_dot_sparse");
 }
 
 template <typename T>
@@ -206,6 +242,18 @@ lak_status launch_axpby_strided(lak_dtype dt, void *x, int64_t incx, double alph
     case LAK_F16: return axpby_strided_t<__half>(x, incx, alpha, y, incy, beta, z, incz, n, grid, block, s);
     }
     return fail(LAK_EDTYPE, "vec_axpby_strided: unknown dtype %d", (int)dt);
+}
+
+lak_status launch_dot_sparse(lak_dtype dt, void *out, const void *vals, const int32_t *idx,
+                             const void *y, int64_t nnz, void *ws, const Launch &L, int64_t head,
+                             cudaStream_t s) {
+    switch (dt) {
+    case LAK_F32: return dot_sparse_t<float>(out, vals, idx, y, nnz, head, ws, L, s);
+    case LAK_F64: return dot_sparse_t<double>(out, vals, idx, y, nnz, head, ws, L, s);
+    case LAK_BF16: return dot_sparse_t<__nv_bfloat16>(out, vals, idx, y, nnz, head, ws, L, s);
+    case LAK_F16: return dot_sparse_t<__half>(out, vals, idx, y, nnz, head, ws, L, s);
+    }
+    return fail(LAK_EDTYPE, "vec_dot_sparse: unknown dtype %d", (int)dt);
 }
 
 lak_status launch_axpy_norm2(lak_dtype dt, void *x, const void *y, const void *z, double alpha,

@@ -606,6 +606,60 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n, l
     return launch_dot(dtype, out, x, y, n, workspace, p.L, p.head, s);
 }
 
+LAK_API size_t vec_dot_sparse_workspace(int64_t nnz, lak_dtype dtype, const lak_cfg *cfg) {
+    return vec_dot_workspace(nnz, dtype, cfg);
+}
+
+LAK_API lak_status vec_dot_sparse(void *out, const void *vals, const int32_t *idx, const void *y,
+                                  int64_t nnz, int64_t n, lak_dtype dtype, void *workspace,
+                                  size_t ws_bytes, const lak_cfg *cfg, void *stream) {
+    lak_status st = common_checks("vec_dot_sparse", dtype, cfg);
+    if (st != LAK_OK) return st;
+    if (nnz < 0 || n < 0) return fail(LAK_EINVAL, "vec_dot_sparse: negative size");
+    if (!out) return fail(LAK_EINVAL, "vec_dot_sparse: NULL out");
+    const int out_bytes = dtype == LAK_F64 ? 8 : 4;
+    if ((uintptr_t)out % out_bytes) return fail(LAK_EINVAL, "vec_dot_sparse: out misaligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nnz == 0) {
+        const cudaError_t e = cudaMemsetAsync(out, 0, out_bytes, s);
+        if (e != cudaSuccess)
+            return fail(LAK_ECUDA, "vec_dot_sparse: memset: %s", cudaGetErrorString(e));
+        return LAK_OK;
+    }
+    const int es = esize(dtype);
+    if (!vals || !idx || !y || n == 0) return fail(LAK_EINVAL, "vec_dot_sparse: NULL pointer or n = 0");
+    if (!aligned_elem(vals, es) || !aligned_elem(y, es) || (uintptr_t)idx % 4)
+        return fail(LAK_EINVAL, "vec_dot_sparse: pointers not aligned to the element size");
+    // the dot's configuration; the widest vec (<= 8) for which one prologue
+    // aligns both the values and the indices
+    VecPlan p;
+    st = plan_vector(LAK_OP_DOT, dtype, nnz, cfg, nullptr, 0, &p);
+    if (st != LAK_OK) return st;
+    int vec = p.L.vec > 8 ? 8 : p.L.vec;
+    int64_t head = 0;
+    for (; vec > 1; vec >>= 1) {
+        const int wv = access_bytes(vec, es), wi = access_bytes(vec, 4);
+        const int64_t h = (int64_t)((wv - (uintptr_t)vals % wv) % wv) / es;
+        if (((uintptr_t)idx + 4 * h) % wi == 0) {
+            head = h < nnz ? h : nnz;
+            break;
+        }
+    }
+    if (vec == 1) head = 0;
+    if (vec != p.L.vec) {
+        lak_cfg c{p.L.block, cfg && cfg->block ? cfg->grid : 0, vec, p.L.inc};
+        st = plan_vector(LAK_OP_DOT, dtype, nnz, &c, nullptr, 0, &p);
+        if (st != LAK_OK) return st;
+    }
+    const size_t need = (size_t)LAK_WS_COUNTER_BYTES + 8 * (size_t)p.L.grid;
+    if (!workspace || ws_bytes < need)
+        return fail(LAK_EWORKSPACE, "vec_dot_sparse: workspace of %zu bytes needed, %zu given", need,
+                    workspace ? ws_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256)
+        return fail(LAK_EWORKSPACE, "vec_dot_sparse: workspace not 256-byte aligned");
+    return launch_dot_sparse(dtype, out, vals, idx, y, nnz, workspace, p.L, head, s);
+}
+
 LAK_API lak_status vec_dot_compensated(double *out, const void *x, const void *y, int64_t n,
                                        lak_dtype dtype, void *workspace, size_t ws_bytes,
                                        const lak_cfg *cfg, void *stream) {

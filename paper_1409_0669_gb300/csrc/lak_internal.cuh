@@ -86,6 +86,9 @@ lak_status launch_axpby(lak_dtype dt, void *x, double alpha, const void *y, doub
 lak_status launch_axpby_strided(lak_dtype dt, void *x, int64_t incx, double alpha, const void *y,
                                 int64_t incy, double beta, const void *z, int64_t incz, int64_t n,
                                 int grid, int block, cudaStream_t s);
+lak_status launch_dot_sparse(lak_dtype dt, void *out, const void *vals, const int32_t *idx,
+                             const void *y, int64_t nnz, void *ws, const Launch &L, int64_t head,
+                             cudaStream_t s);
 lak_status launch_axpy_norm2(lak_dtype dt, void *x, const void *y, const void *z, double alpha,
                              void *out, int64_t n, void *ws, const Launch &L, int64_t head,
                              cudaStream_t s);
@@ -298,6 +301,47 @@ template <typename T> __device__ __forceinline__ T ld_cached(const T *p) { retur
 template <typename A> __device__ __forceinline__ A group_sum(A v, int width) {
     for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Deterministic sum over the whole grid of one value per thread, written to
+// *out: a warp reduction in A, FP64 across the block's warps into one partial
+// per block, and the last block to arrive (ticket on *counter, which wraps
+// back to 0 for the next launch) adds the partials in block order.  Every
+// thread of every block must call it, as the kernel's last action.
+template <typename A, typename OutT>
+__device__ __forceinline__ void grid_sum_last_block(A v, OutT *out, unsigned int *counter,
+                                                    double *partials) {
+    __shared__ double wsum[32];
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    const A s = group_sum(v, 32);
+    if (lane == 0) wsum[warp] = (double)s;
+    __syncthreads();
+    if (warp == 0) {
+        double b = lane < nwarps ? wsum[lane] : 0.0;
+        b = group_sum(b, 32);
+        if (lane == 0) {
+            partials[blockIdx.x] = b;
+            __threadfence();
+            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
+            am_last = (ticket == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + b);
+    t = group_sum(t, 32);
+    if (lane == 0) wsum[warp] = t;
+    __syncthreads();
+    if (warp == 0) {
+        double f = lane < nwarps ? wsum[lane] : 0.0;
+        f = group_sum(f, 32);
+        if (lane == 0) *out = static_cast<OutT>(f);
+    }
 }
 
 }  // namespace lak

@@ -68,3 +68,20 @@ def launch_time_us(fn: Callable[[], None], reps: int, flush: Optional[torch.Tens
             t_b = _interval_ms(pairs, stream)
             diffs.append(t_b - t_f)
     return max(statistics.median(diffs) * 1e3 / reps, 0.0)
+
+
+def warm_time_us(fn: Callable[[], None], reps: int, stream=None) -> float:
+    """Device time of one call of `fn` with its operands left in L2 by the
+    previous call: `reps` calls back to back in one event interval (after one
+    call to warm L2), in microseconds."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    reps = max(int(reps), 1)
+
+    def calls():
+        for _ in range(reps):
+            fn()
+
+    with torch.cuda.stream(stream):
+        fn()
+        return _interval_ms(calls, stream) * 1e3 / reps
