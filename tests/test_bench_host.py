@@ -78,20 +78,31 @@ def test_watched_items_and_roofline():
     assert abs(bench.flops_of(items[5]) / 2 - 14581760) < 1
 
 
-def test_recorded_traffic_requires_unchanged_source(tmp_path):
+def test_recorded_traffic_requires_unchanged_sources_and_cfg(tmp_path, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
-    src = tmp_path / "k.cu"
-    src.write_text("kernel v1")
-    import hashlib
-    rec = {"k": {"dram_bytes": 123, "source": str(src),
-                 "sha256": hashlib.sha256(b"kernel v1").hexdigest()}}
+
+    class It:
+        name, op = "gemv_row_f64_16384", "gemv_row"
+    state = {"digest": "d1", "cfg": [64, 0, 4, 0]}
+    monkeypatch.setattr(bench, "_sources_digest", lambda op: state["digest"])
+    monkeypatch.setattr(bench, "_item_cfg", lambda it: list(state["cfg"]))
+    rec = {It.name: {"dram_bytes": 123, "sources_sha256": "d1", "cfg": [64, 0, 4, 0]}}
     path = tmp_path / "t.json"
     path.write_text(json.dumps(rec))
-    assert bench.recorded_traffic(str(path), "k") == 123
-    src.write_text("kernel v2")
-    assert bench.recorded_traffic(str(path), "k") is None
-    assert bench.recorded_traffic(str(path), "missing") is None
+    assert bench.recorded_traffic(str(path), It) == 123
+    state["digest"] = "d2"                       # a kernel source changed
+    assert bench.recorded_traffic(str(path), It) is None
+    state["digest"], state["cfg"] = "d1", [128, 0, 2, 0]   # another launch shape
+    assert bench.recorded_traffic(str(path), It) is None
+
+    class Missing:
+        name, op = "missing", "copy"
+    assert bench.recorded_traffic(str(path), Missing) is None
+    # every op the sweep launches has its kernel sources listed, and they exist
+    for op in ("copy", "axpy", "dot", "gemv_row", "gemv_col", "spmv"):
+        for rel in bench.TRAFFIC_SOURCES[op]:
+            assert os.path.exists(os.path.join(ROOT, rel)), rel
 
 
 def test_reference_arm_runs_only_on_rank0(monkeypatch, capsys):
