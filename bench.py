@@ -827,6 +827,8 @@ def run_profile_set(device):
         pat = ag.CsrPattern(rpd, cid, nc)
         cp, ri, perm = pat.transpose()
         rec(f"gather_{nm}_f32", nnz * 12, lambda: lak.vec_gather(vd, perm, out=dv))
+        rec(f"dot_sparse_{nm}_f32", nnz * 8,
+            lambda: lak.vec_dot_sparse(vd, cid, xs, out=out, workspace=ws))
         del S
     ns = synth.log_uniform_ints(512, 65_536, 1_048_576, 1308)
     bx = [torch.empty(int(k), device=dev) for k in ns]
@@ -834,6 +836,14 @@ def run_profile_set(device):
     bz = [synth.device_uniform_(torch.empty(int(k), device=dev), 1310) for k in ns]
     bt = B.axpy_batch(bx, byy, bz, [0.5] * len(ns))
     rec("batch_axpy_f32", 12 * int(sum(int(k) for k in ns)), bt.run)
+    gm = synth.log_uniform_ints(256, 64, 4096, 1311)
+    gn = synth.log_uniform_ints(256, 64, 4096, 1312)
+    gA = [synth.device_normal_(torch.empty(int(a), int(b), device=dev), 1313) for a, b in zip(gm, gn)]
+    gx = [synth.device_uniform_(torch.empty(int(b), device=dev), 1314) for b in gn]
+    gy = [torch.empty(int(a), device=dev) for a in gm]
+    bg = B.gemv_batch(gA, gx, gy)
+    rec("batch_gemv_f32", 4 * int(sum(int(a) * int(b) + int(a) + int(b) for a, b in zip(gm, gn))),
+        bg.run)
     torch.cuda.synchronize()
     print(json.dumps({"profile_set": launches}))
     return 0
