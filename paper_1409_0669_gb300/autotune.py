@@ -317,6 +317,8 @@ def _main(argv=None):
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--top", type=int, default=15)
     ap.add_argument("--study", action="store_true", help="copy-first transfer study")
+    ap.add_argument("--paper-sizes", action="store_true",
+                    help="run the study at the paper's sizes (2e6-entry vectors, 2048^2)")
     ap.add_argument("--buckets", action="store_true",
                     help="one configuration per size bucket from the comma-separated --size list")
     ap.add_argument("--out", default=None)
@@ -332,9 +334,16 @@ def _main(argv=None):
                            "cache": {f"{args.op}:{args.storage}:{b}": v["cfg"]
                                      for b, v in per.items()}}, indent=1)
     elif args.study:
-        sizes = {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
-                 "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"}
+        if args.paper_sizes:
+            # the paper's own problem sizes (vectors of 2e6 entries, a 2048^2 matrix);
+            # the CSR product, which the paper leaves out, on the 64^3 Laplacian
+            sizes = {"copy": 2_000_000, "axpy": 2_000_000, "dot": 2_000_000,
+                     "gemv_row": 2048, "gemv_col": 2048, "spmv": "lap3d_64"}
+        else:
+            sizes = {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
+                     "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"}
         rep = copy_first_study(args.storage, sizes, reps=args.reps)
+        rep["sizes"] = sizes
         text = json.dumps(rep, indent=1)
     else:
         res = tune(args.op, args.storage, size, args.reps)
