@@ -69,14 +69,22 @@ spmv_kernel(T *__restrict__ y, const int32_t *__restrict__ rp, const int32_t *__
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int64_t kk = k + (int64_t)u * G;
-                    if (kk < k1) acc[u] = fma_acc(widen(val[u]), widen(ld_cached(x + col[u])), acc[u]);
+                    // FP64: one chain (GB300's FP64 pipe, not latency, is the limit,
+                    // and U partial sums would cost U - 1 extra adds per row)
+                    constexpr bool one_chain = sizeof(Ac) == 8;
+                    if (kk < k1) {
+                        Ac &a = one_chain ? acc[0] : acc[u];
+                        a = fma_acc(widen(val[u]), widen(ld_cached(x + col[u])), a);
+                    }
                 }
             }
         }
+        if constexpr (sizeof(Ac) != 8) {
 #pragma unroll
-        for (int w = 1; w < U; w <<= 1) {
+            for (int w = 1; w < U; w <<= 1) {
 #pragma unroll
-            for (int u = 0; u + w < U; u += 2 * w) acc[u] += acc[u + w];
+                for (int u = 0; u + w < U; u += 2 * w) acc[u] += acc[u + w];
+            }
         }
         const Ac s = group_sum(acc[0], G);
         if (lg == 0 && row < row_end) y[row] = narrow<T>(s);
