@@ -71,6 +71,7 @@ def _bind(path: str):
         "orc_axpby": (None, [_F64P, ctypes.c_double, _F64P, ctypes.c_double, _F64P, _I64]),
         "orc_dot": (ctypes.c_double, [_F64P, _F64P, _I64, _F64P]),
         "orc_sparse_dot": (ctypes.c_double, [_F64P, _I32P, _F64P, _I64]),
+        "orc_csr_row_bins": (None, [_I32P, _I64, _I64, _I64, _I32P, _I64P]),
         "orc_scale": (None, [_F64P, _F64P, ctypes.c_double, _I64]),
         "orc_gemv": (None, [_F64P, _F64P, _F64P, _I64, _I64, _I64, ctypes.c_int]),
         "orc_gemv_entry": (ctypes.c_double, [_F64P, _F64P, _I64, _I64, _I64, ctypes.c_int]),
@@ -253,6 +254,18 @@ def csr_to_csc(row_ptr, col_idx, n: int):
     if rc != 0:
         raise MemoryError("oracle csr_to_csc: allocation failed")
     return col_ptr, row_idx[:nnz], perm[:nnz]
+
+
+def csr_row_bins(row_ptr, per_lane: int = 8, nbins: int = 7):
+    """Row-binned CSR: (perm, bin_ptr) -- rows grouped by length bin, stable
+    within a bin; see lak_oracle.c for the bin rule."""
+    rp = _i32(row_ptr)
+    m = rp.size - 1
+    perm = np.empty(max(m, 1), np.int32)
+    bptr = np.empty(nbins + 1, np.int64)
+    _load().orc_csr_row_bins(_ptr(rp, _I32P), m, per_lane, nbins, _ptr(perm, _I32P),
+                             _ptr(bptr, _I64P))
+    return perm[:m], bptr
 
 
 def csr_to_sell(row_ptr, col_idx, C: int = 32, sigma: int = 1):

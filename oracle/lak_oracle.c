@@ -228,6 +228,41 @@ int orc_csr_to_csc(int32_t *col_ptr, int32_t *row_idx, int64_t *perm,
 /* ---- sliced ELLPACK (SELL-C-sigma) ----------------------------------------- */
 
 /*
+ * Row-binned CSR: the rows of an m-row CSR pattern grouped by length.  Row i
+ * with L = row_ptr[i+1] - row_ptr[i] stored entries falls in bin b, the
+ * smallest b < nbins - 1 with L <= per_lane * 2^b, else in the last bin (rows
+ * longer than per_lane * 2^(nbins-2)).  perm lists the rows bin by bin, in
+ * increasing row index within a bin (a stable sort by bin); bin_ptr[b] is the
+ * position of bin b's first row (bin_ptr[nbins] = m).  The product over the
+ * binned rows is the CSR product itself (orc_csr_spmv).
+ */
+static int64_t row_bin(int64_t len, int64_t per_lane, int64_t nbins)
+{
+    int64_t b = 0;
+    while (b < nbins - 1 && len > (per_lane << b)) ++b;
+    return b;
+}
+
+void orc_csr_row_bins(const int32_t *row_ptr, int64_t m, int64_t per_lane, int64_t nbins,
+                      int32_t *perm, int64_t *bin_ptr)
+{
+    for (int64_t b = 0; b <= nbins; ++b) bin_ptr[b] = 0;
+    /* bin of every row, counted */
+    for (int64_t i = 0; i < m; ++i)
+        bin_ptr[row_bin((int64_t)row_ptr[i + 1] - row_ptr[i], per_lane, nbins) + 1] += 1;
+    for (int64_t b = 0; b < nbins; ++b) bin_ptr[b + 1] += bin_ptr[b];
+    /* place rows in increasing index order within each bin */
+    int64_t *next = (int64_t *)malloc((size_t)(nbins > 0 ? nbins : 1) * sizeof(int64_t));
+    if (!next) return;
+    for (int64_t b = 0; b < nbins; ++b) next[b] = bin_ptr[b];
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t b = row_bin((int64_t)row_ptr[i + 1] - row_ptr[i], per_lane, nbins);
+        perm[next[b]++] = (int32_t)i;
+    }
+    free(next);
+}
+
+/*
  * SELL-C-sigma layout of an m-row CSR pattern with slices of C rows: within
  * every window of `sigma` consecutive rows (sigma a multiple of C, or 1 for no
  * sorting) rows are ordered by decreasing length, ties by increasing row index;

@@ -434,6 +434,40 @@ def pin_sell_spmv_matches_csr_and_eigen():
 
 # ---- derivatives --------------------------------------------------------------------
 
+def pin_csr_row_bins_bruteforce():
+    """Row-binned CSR layout against an independent statement of the rule: bin =
+    ceil(log2(L / per_lane)) clipped to [0, nbins-1] (exact integer form), rows
+    listed bin by bin in increasing index -- checked as a permutation, per-bin
+    length bounds, stability and counts, on patterns with empty rows and rows
+    at every bin edge."""
+    for seed, per_lane, nbins in ((60, 8, 7), (61, 4, 7), (62, 8, 3), (63, 1, 2)):
+        g = synth.rng(seed)
+        lens = list(g.integers(0, 300, 400))
+        edges = [0, per_lane, per_lane + 1] + [per_lane << k for k in range(nbins)] + \
+                [(per_lane << k) + 1 for k in range(nbins)]
+        lens = edges + lens
+        rp = np.zeros(len(lens) + 1, np.int64)
+        rp[1:] = np.cumsum(lens)
+        perm, bptr = oracle.csr_row_bins(rp.astype(np.int32), per_lane, nbins)
+
+        def bin_of(L):
+            b = 0
+            while per_lane * (1 << b) < L:          # smallest b with L <= per_lane * 2^b
+                b += 1
+            return min(b, nbins - 1)
+        want = sorted(range(len(lens)), key=lambda i: (bin_of(lens[i]), i))
+        assert list(perm) == want
+        assert sorted(perm) == list(range(len(lens)))
+        for b in range(nbins):
+            rows = perm[bptr[b]:bptr[b + 1]]
+            assert list(rows) == sorted(rows)
+            assert all(bin_of(lens[r]) == b for r in rows)
+        assert bptr[0] == 0 and bptr[nbins] == len(lens)
+    # degenerate: no rows
+    perm, bptr = oracle.csr_row_bins(np.zeros(1, np.int32), 8, 7)
+    assert perm.size == 0 and list(bptr) == [0] * 8
+
+
 def pin_dense_outer_fd():
     # L(A) = <w, A x>  =>  dL/dA = w x^T; central differences are exact up to
     # rounding for a linear map.
@@ -547,6 +581,7 @@ PINS = [
     pin_spmv_golden, pin_spmv_laplacian_ones, pin_spmv_eigen_2d, pin_spmv_eigen_3d,
     pin_spmv_dense_bruteforce, pin_spmv_rows, pin_csc_transpose,
     pin_sell_layout_bruteforce, pin_sell_spmv_matches_csr_and_eigen,
+    pin_csr_row_bins_bruteforce,
     pin_dense_outer_fd, pin_sampled_outer_fd, pin_scale_dot_gradient,
     pin_round_bf16, pin_round_f16, pin_round_f32,
 ]

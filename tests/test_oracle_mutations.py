@@ -29,6 +29,9 @@ MUTANTS = [
      "acc_add_prod(&acc, v[k], y[k < nnz ? c[0] : 0]);"),
     ("sparse_dot_drop_last", "for (int64_t k = 0; k < nnz; ++k) acc_add_prod(&acc, v[k], y[c[k]]);",
      "for (int64_t k = 0; k + 1 < nnz; ++k) acc_add_prod(&acc, v[k], y[c[k]]);"),
+    ("row_bins_edge_inclusive", "while (b < nbins - 1 && len > (per_lane << b)) ++b;",
+     "while (b < nbins - 1 && len >= (per_lane << b)) ++b;"),
+    ("row_bins_unstable", "perm[next[b]++] = (int32_t)i;", "perm[bin_ptr[b + 1] - 1 - (next[b]++ - bin_ptr[b])] = (int32_t)i;"),
     ("gemv_row_transposed",
      "double a = (layout == 0) ? A[i * lda + j] : A[i + j * lda];\n            acc_add_prod(&acc, a, x[j]);\n        }\n        y[i]",
      "double a = (layout == 0) ? A[j * lda + i] : A[i + j * lda];\n            acc_add_prod(&acc, a, x[j]);\n        }\n        y[i]"),
