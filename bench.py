@@ -709,16 +709,18 @@ def run_fused(device, reps=20):
 
 
 def run_formats(device, reps=20):
-    """CSR vs SELL-C-sigma (C = 32) on the sweep's two matrices (3D Laplacian
-    128^3 with sigma = 1, power-law 2M rows with sigma = 1024), FP32 and FP64,
-    L2 flushed (256 MB read) before every timed launch; SELL bytes count the
-    padded slots it actually reads.  Conversion time is reported once."""
+    """CSR vs SELL-C-sigma (C = 32) vs row-binned CSR on the sweep's two
+    matrices (3D Laplacian 128^3 with sigma = 1, power-law 2M rows with sigma =
+    1024), FP32 and FP64, L2 flushed (256 MB read) before every timed launch;
+    SELL bytes count the padded slots it actually reads, the binned product
+    reads the CSR bytes plus its row permutation.  Conversion times once."""
     import time
 
     import torch
 
     import paper_1409_0669_gb300 as lak
     import synth
+    from paper_1409_0669_gb300.csr_bin import BinnedCsr
     from paper_1409_0669_gb300.sell import SellMatrix
 
     dev = device
@@ -753,13 +755,28 @@ def run_formats(device, reps=20):
             fc = (lambda: lak.csr_spmv(rpd, cid, vd, x, y=y))
             fc()
             tc = _launch_ms(fc, reps, flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Bm = BinnedCsr(rpd, cid, vd, ncols)
+            torch.cuda.synchronize()
+            bin_build_ms = (time.perf_counter() - t0) * 1e3
+            fb = (lambda: Bm.spmv(x, y=y))
+            fb()
+            tb = _launch_ms(fb, reps, flush)
+            bins = Bm.bin_ptr.cpu().tolist()
+            del Bm
             out[f"{name}_{storage}"] = {
                 "csr_us": round(tc * 1e3, 2), "csr_GBs": round(csr_bytes / (tc * 1e-3) / 1e9, 1),
                 "sell_us": round(best[0] * 1e3, 2), "sell_cfg": list(best[1]),
                 "sell_GBs_csr_bytes": round(csr_bytes / (best[0] * 1e-3) / 1e9, 1),
                 "sell_padding": round(A.total / max(nnz, 1) - 1, 4), "sigma": sigma,
                 "speedup_vs_csr": round(tc / best[0], 3), "conversion_ms": round(conv_ms, 2),
-                "sell_bytes_read": sell_bytes}
+                "sell_bytes_read": sell_bytes,
+                "binned_us": round(tb * 1e3, 2),
+                "binned_GBs_csr_bytes": round(csr_bytes / (tb * 1e-3) / 1e9, 1),
+                "binned_speedup_vs_csr": round(tc / tb, 3),
+                "binned_build_ms": round(bin_build_ms, 2), "binned_rows_per_bin":
+                    [bins[i + 1] - bins[i] for i in range(len(bins) - 1)]}
             del A
     return out
 

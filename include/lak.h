@@ -231,6 +231,35 @@ LAK_API lak_status vec_dot(void *out, const void *x, const void *y, int64_t n,
                            const lak_cfg *cfg, void *stream);
 
 /*
+ * Row-binned CSR (an SpMV format variant; the paper leaves sparse formats out,
+ * Sec. 1).  The CSR arrays are used as they are; a row permutation groups the
+ * rows by length.  Row i with L stored entries falls in bin b, the smallest
+ * b < LAK_CSR_BINS - 1 with L <= LAK_CSR_BIN_PER_LANE * 2^b, else in the last
+ * bin.  perm (m int32, device) lists the rows bin by bin, in increasing row
+ * index within a bin; bin_ptr (LAK_CSR_BINS + 1 int64, device) holds each
+ * bin's first position, bin_ptr[LAK_CSR_BINS] = m.
+ *
+ * csr_bin_build computes perm and bin_ptr from row_ptr on the device (three
+ * kernels; workspace >= csr_bin_workspace(m) bytes, 256-byte aligned, no
+ * zeroing needed).  csr_bin_spmv computes y = A x in one launch: rows of bin b
+ * get 2^min(b, 5) lanes each (all of a bin's rows need one step of at most
+ * LAK_CSR_BIN_PER_LANE loads per lane, except the last bin's, which loop), so
+ * every warp serves rows of similar length.  Each y[i] is written once; the
+ * result is deterministic.  cfg: block and grid only (0 = automatic).
+ * Requirements the library does not check on the device: perm and bin_ptr
+ * from csr_bin_build for this row_ptr, and the CSR requirements of csr_spmv.
+ */
+#define LAK_CSR_BINS 7
+#define LAK_CSR_BIN_PER_LANE 4
+LAK_API size_t csr_bin_workspace(int64_t m);
+LAK_API lak_status csr_bin_build(int32_t *perm, int64_t *bin_ptr, const int32_t *row_ptr,
+                                 int64_t m, void *workspace, size_t ws_bytes, void *stream);
+LAK_API lak_status csr_bin_spmv(void *y, const int32_t *row_ptr, const int32_t *col_idx,
+                                const void *vals, const void *x, const int32_t *perm,
+                                const int64_t *bin_ptr, int64_t m, int64_t n, int64_t nnz,
+                                lak_dtype dtype, const lak_cfg *cfg, void *stream);
+
+/*
  * vec_dot_sparse: *out = sum_{k<nnz} vals[k] * y[idx[k]] -- the inner product
  * of Sec. 2 with one operand given by its nonzeros: a sparse vector of nnz
  * stored values `vals` at positions `idx` (int32) times a dense vector y of n

@@ -24,7 +24,7 @@ OPS = {"copy": 0, "axpy": 1, "dot": 2, "gemv_row": 3, "gemv_col": 4, "spmv": 5}
 # exported symbols, in header order (checked by the ABI test)
 EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_resolve_cfg",
            "lak_size_bucket", "lak_set_default_cfg_bucket", "vec_dot_sparse_workspace",
-           "vec_dot_sparse",
+           "vec_dot_sparse", "csr_bin_workspace", "csr_bin_build", "csr_bin_spmv",
            "vec_copy", "vec_axpy", "vec_axpby", "vec_axpby_strided", "vec_axpy_norm2_workspace",
            "vec_axpy_norm2", "vec_dot_workspace", "vec_dot", "vec_dot_compensated",
            "vec_dot_noalloc",
@@ -104,6 +104,9 @@ _SIGNATURES = {
     "vec_dot_workspace": (_SZ, [_I64, _I32, _CFGP]),
     "vec_dot": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "vec_dot_sparse_workspace": (_SZ, [_I64, _I32, _CFGP]),
+    "csr_bin_workspace": (_SZ, [_I64]),
+    "csr_bin_build": (_I32, [_P, _P, _P, _I64, _P, _SZ, _P]),
+    "csr_bin_spmv": (_I32, [_P, _P, _P, _P, _P, _P, _P, _I64, _I64, _I64, _I32, _CFGP, _P]),
     "vec_dot_sparse": (_I32, [_P, _P, _P, _P, _I64, _I64, _I32, _P, _SZ, _CFGP, _P]),
     "vec_dot_noalloc": (_I32, [_P, _P, _P, _I64, _I32, _CFGP, _P]),
     "vec_dot_compensated": (_I32, [_P, _P, _P, _I64, _I32, _P, _SZ, _CFGP, _P]),
