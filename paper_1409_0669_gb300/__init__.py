@@ -70,8 +70,15 @@ def storage_of(t: torch.Tensor) -> str:
         raise TypeError(f"unsupported dtype {t.dtype}; expected float32/float64/bfloat16/float16")
 
 
+# The current stream's raw handle without building a torch Stream object (the
+# public call costs ~3 us per launch, more than the launch itself).
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream) -> int:
     if stream is None:
+        if _raw_stream is not None:
+            return _raw_stream(torch.cuda.current_device())
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream
@@ -146,6 +153,22 @@ def set_default_cfg(op: str, storage: str, cfg: CfgLike, bucket: Optional[int] =
     b = -1 if bucket is None else int(bucket)
     _native.check("lak_set_default_cfg",
                   _lib.lak_set_default_cfg_bucket(OPS[op], DTYPES[storage], b, _cfg_ptr(cfg)))
+    _dot_ws_sizes.clear()                 # workspace needs follow the defaults
+
+
+# vec_dot_workspace(n, storage) for calls without an explicit cfg, memoised
+# (cleared whenever a default configuration changes)
+_dot_ws_sizes = {}
+
+
+def _dot_ws_need(n: int, storage: str, cfg: CfgLike) -> int:
+    if cfg is not None:
+        return vec_dot_workspace(n, storage, cfg)
+    key = (n, storage, torch.cuda.current_device())
+    need = _dot_ws_sizes.get(key)
+    if need is None:
+        need = _dot_ws_sizes[key] = vec_dot_workspace(n, storage)
+    return need
 
 
 def vec_copy(x: torch.Tensor, y: torch.Tensor, cfg: CfgLike = None, stream=None) -> torch.Tensor:
@@ -241,9 +264,8 @@ def vec_dot(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None
     elif out.dtype != odt or out.numel() < 1:
         raise TypeError(f"out must be a {odt} tensor with at least one element")
     sh = _stream(stream)
-    need = vec_dot_workspace(n, s, cfg)
     if workspace is None:
-        workspace = _workspace(need, sh, x.device)
+        workspace = _workspace(_dot_ws_need(n, s, cfg), sh, x.device)
     st = _lib.vec_dot(_dev_ptr(out, "out"), _vec_arg(x, "x"), _vec_arg(y, "y"), n, DTYPES[s],
                       _dev_ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                       _cfg_ptr(cfg), sh)
@@ -300,9 +322,8 @@ def vec_dot_compensated(x: torch.Tensor, y: torch.Tensor, out: Optional[torch.Te
     elif out.dtype != torch.float64 or out.numel() < 1:
         raise TypeError("out must be a float64 tensor with at least one element")
     sh = _stream(stream)
-    need = vec_dot_workspace(n, s, cfg)
     if workspace is None:
-        workspace = _workspace(need, sh, x.device)
+        workspace = _workspace(_dot_ws_need(n, s, cfg), sh, x.device)
     st = _lib.vec_dot_compensated(_dev_ptr(out, "out"), _vec_arg(x, "x"), _vec_arg(y, "y"), n,
                                   DTYPES[s], _dev_ptr(workspace, "workspace"),
                                   workspace.numel() * workspace.element_size(), _cfg_ptr(cfg), sh)
