@@ -1,26 +1,25 @@
 // CSR sparse matrix-vector product y = A x (the textbook product; the paper
-// leaves sparse formats out of its study, Sec. 1).
+// leaves sparse formats out of its study, Sec. 1).  Two kernels, three
+// variants chosen on the host from the mean row length:
 //
-// Short rows -- warp-stream variant.  A warp owns 32 consecutive rows, whose
-// stored entries form one contiguous range [row_ptr[r0], row_ptr[r0+32]).  The
-// warp walks that range in chunks of 32*U entries: lane l loads entries
-// chunk + u*32 + l (u < U) -- every load instruction covers 32 consecutive
-// entries -- gathers x[col], and writes the products to its warp's slice of
-// shared memory.  Then lane l adds the products that belong to its own row, in
-// entry order, into a register.  All global loads are coalesced whatever the
-// row lengths, and the work per warp is proportional to its entries.
+// Group per row (spmv_kernel): a group of G lanes (a power of two <= 32) owns
+// one row; the lanes stride through the row's stored entries G at a time,
+// each issuing U independent loads per step before using any of them,
+// multiply by the gathered x[col] (cached load: neighbouring rows share x
+// entries), and the group reduces with shuffles.  Short rows (stencils, mean
+// <= 12) take one or two lanes per row with U covering the row, so a warp
+// keeps 16-32 rows' loads in flight; their col_idx / vals loads are strided
+// across the warp and go through L1 (one miss brings the lines the next lanes
+// need).  Long rows (mean > 64) take more lanes per row and stream col_idx /
+// vals past L1.  In FP64 each lane keeps one accumulator chain.
 //
-// Long rows -- vector variant:
-// a group of G lanes (G a power of two <= 32, chosen on the host from the mean
-// row length) owns one row: the lanes stride through the row's stored entries
-// G at a time, each issuing U independent loads per step before using any of
-// them, multiply by the gathered x[col] (cached load: neighbouring rows share x
-// entries), and the group reduces with shuffles.  Short rows (the Laplacian
-// stencils) take one or two lanes per row with U covering the whole row, so a
-// warp keeps 32 rows' worth of loads in flight; their col_idx / vals loads are
-// strided across the warp, so they go through L1 (one miss brings the lines
-// the neighbouring lanes need next).  Long rows use more lanes per row and
-// stream col_idx / vals past L1.
+// Warp-segmented (spmv_seg_kernel, 13 <= mean <= 64): a warp owns 32
+// consecutive rows, whose entries are contiguous, and walks them in chunks of
+// 32*U entries with coalesced (16-byte when aligned) loads; rows that cross
+// lanes are joined by a segmented shuffle scan, rows that cross chunks in a
+// per-warp shared accumulator with one writer per row per chunk -- no atomics,
+// deterministic (the body lives in spmv_seg.cuh, shared with the batched
+// kernel).
 #include "lak_internal.cuh"
 #include "spmv_seg.cuh"
 
