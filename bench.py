@@ -1248,6 +1248,18 @@ def run_gb300(args):
         summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
                         "us": round(t * 1e3, 2), "bound": b["bound"],
                         "frac_bound": round(b["frac"], 4)}
+    # the copy kernel moving the same number of bytes (cold): the streaming
+    # ceiling at that size, launch and DRAM-latency ramp included
+    with torch.cuda.stream(stream):
+        copy_same = copy_at_bytes([it.nbytes for it, _ in per.values()], device, lak)
+    for key, v in summary.items():
+        it = next((it for name, (it, _) in per.items()
+                   if (f"{it.op}_{name.split('_')[1]}_{it.dtype}" if it.op == "spmv"
+                       else f"{it.op}_{it.dtype}") == key and it.size == v["size"]), None)
+        if it is not None and it.nbytes in copy_same:
+            c = copy_same[it.nbytes]
+            v["copy_same_bytes_GBs"] = round(c, 1)
+            v["frac_copy_same_bytes"] = round(v["GBs"] / c, 4)
     # CSR SpMV: the floor set by its x gather -- the sparse inner product over
     # the matrix's own entries (vec_dot_sparse) timed alone
     with torch.cuda.stream(stream):
@@ -1268,8 +1280,13 @@ def run_gb300(args):
                  "gemv_row_f64_2048"):
         if name in per:
             it, t = per[name]
-            summary["paper_point_" + name] = {"GBs": round(it.nbytes / (t * 1e-3) / 1e9, 1),
-                                              "us": round(t * 1e3, 2)}
+            gbs = it.nbytes / (t * 1e-3) / 1e9
+            summary["paper_point_" + name] = {"GBs": round(gbs, 1), "us": round(t * 1e3, 2)}
+            if it.nbytes in copy_same:
+                summary["paper_point_" + name]["copy_same_bytes_GBs"] = round(
+                    copy_same[it.nbytes], 1)
+                summary["paper_point_" + name]["frac_copy_same_bytes"] = round(
+                    gbs / copy_same[it.nbytes], 4)
 
     if args.sweep_json:
         rows = [{"name": n, "op": it.op, "dtype": it.dtype, "size": it.size, "bytes": it.nbytes,
@@ -1347,6 +1364,28 @@ def run_gb300(args):
         dist.destroy_process_group()
     del keep
     return 0
+
+
+def copy_at_bytes(sizes, device, lak, reps=10):
+    """GB/s of vec_copy (FP32) moving each of the given byte counts (read +
+    write), L2 cold: {bytes: GB/s}."""
+    import torch
+    from paper_1409_0669_gb300.timing import launch_time_us
+    l2 = torch.cuda.get_device_properties(device).L2_cache_size
+    top = max(sizes)
+    src = torch.empty(top // 8 + 1, dtype=torch.float32, device=device)
+    dst = torch.empty_like(src)
+    src.zero_()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=device)
+    out = {}
+    for b in sorted(set(sizes)):
+        n = b // 8
+        ys, xs = src[:n], dst[:n]
+        lak.vec_copy(xs, ys)
+        us = launch_time_us(lambda: lak.vec_copy(xs, ys), reps, flush if b < 2 * l2 else None)
+        out[b] = 8 * n / (us * 1e-6) / 1e9
+    del src, dst, flush
+    return out
 
 
 def gather_floors(per, lak, reps=20):
