@@ -501,7 +501,8 @@ LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, in
  * floating-point summation (axpy: identical).  The dot keeps at most
  * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).  A NULL cfg
  * (or block 0) takes the batched kernels' own built-in launch shape, not the
- * per-size defaults of the single-instance calls.
+ * per-size defaults of the single-instance calls.  Batched GEMV takes at most
+ * 128 threads per block (LAK_EINVAL otherwise).
  * ---------------------------------------------------------------------- */
 typedef struct { void *x; const void *y; const void *z; int64_t n; double alpha; } lak_axpy_desc;
 typedef struct { void *out; const void *x; const void *y; int64_t n; } lak_dot_desc;

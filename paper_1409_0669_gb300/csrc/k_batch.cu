@@ -210,8 +210,15 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
     }
 }
 
+// At most 128 threads per block and 64 registers per thread: eight blocks per
+// SM.  The kernel wants ~81 registers for 32-byte packs; capped, it spills a few
+// values to L1 but keeps twice the blocks -- and with them twice the loads --
+// in flight (4.0 vs 3.5 TB/s on the 2048-instance mix; the batched GEMV is
+// latency-bound, not arithmetic-bound).
+constexpr int kGemvBatchMaxBlock = 128;
+
 template <typename T, int V>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kGemvBatchMaxBlock, 8)
 gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                   const GemvItem *__restrict__ items) {
     using A = typename Acc<T>::type;
@@ -348,6 +355,9 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
           cfg->vec != 16)))
         return fail(LAK_EINVAL, "lak_batch_plan: invalid cfg");
     const lak_cfg c = batch_config(op, dtype, cfg);
+    if (op == LAK_OP_GEMV_ROW && c.block > kGemvBatchMaxBlock)
+        return fail(LAK_EINVAL, "lak_batch_plan: batched GEMV takes at most %d threads per block",
+                    kGemvBatchMaxBlock);
     int vec = c.vec;
     if (op == LAK_OP_SPMV) vec = vec < 4 ? 4 : (vec > 8 ? 8 : vec);   // seg rows: 4..8 entries
     const int es = esize(dtype);
@@ -500,7 +510,8 @@ LAK_API lak_status lak_batch_run(const lak_batch_info *info, const void *dev_tab
             return fail(LAK_EWORKSPACE, "lak_batch_run: workspace not 256-byte aligned");
     }
     const int block = info->cfg.block;
-    if (block < 32 || block > 512 || block % 32)
+    if (block < 32 || block > 512 || block % 32 ||
+        (info->op == LAK_OP_GEMV_ROW && block > kGemvBatchMaxBlock))
         return fail(LAK_EINVAL, "lak_batch_run: bad block %d", block);
     const DeviceInfo *di = device_info();
     if (!di) return LAK_ECUDA;

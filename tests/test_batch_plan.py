@@ -63,6 +63,14 @@ def test_gemv_rows_per_unit_and_spmv_units(nat):
     assert list(offs) == [0, 1, 2, 4, 20]
 
 
+def test_gemv_plan_rejects_blocks_over_128(nat):
+    g = [nat.GemvDesc(256, 512, 768, 100, 100, 100)]
+    with pytest.raises(AssertionError):
+        plan(nat, "gemv_row", "f32", g, nat.LakCfg(256, 0, 4, 0))
+    info, offs, _ = plan(nat, "gemv_row", "f32", g, nat.LakCfg(128, 0, 4, 0))
+    assert info.cfg.block == 128
+
+
 def test_plan_rejects_bad_input(nat):
     lib = nat.load()
     info = nat.BatchInfo()
