@@ -139,10 +139,10 @@ bin_scatter_kernel(const int32_t *__restrict__ rp, int64_t m, const int32_t *__r
 }
 
 // One step of a lane over its row: up to kE entries k, k + G, ... below k1,
-// all loads issued before any is used.  Indices are 32-bit (m and nnz are
-// below 2^31, checked on the host).
+// all loads issued before any is used.  Entry indices are unsigned 32-bit:
+// nnz < 2^31 (checked on the host), so k + G * kE stays below 2^32.
 template <typename T>
-__device__ __forceinline__ void bin_row_step(typename Acc<T>::type (&acc)[kE], int32_t k, int32_t k1,
+__device__ __forceinline__ void bin_row_step(typename Acc<T>::type (&acc)[kE], uint32_t k, uint32_t k1,
                                              int G, const int32_t *__restrict__ ci,
                                              const T *__restrict__ vals, const T *__restrict__ x) {
     using Ac = typename Acc<T>::type;
@@ -151,7 +151,7 @@ __device__ __forceinline__ void bin_row_step(typename Acc<T>::type (&acc)[kE], i
     T val[kE];
 #pragma unroll
     for (int u = 0; u < kE; ++u) {
-        const int32_t kk = k + u * G;
+        const uint32_t kk = k + (uint32_t)(u * G);
         if (kk < k1) {
             ld_raw<4, CACHED>(&col[u], ci + kk);
             ld_raw<(int)sizeof(T), CACHED>(&val[u], vals + kk);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void bin_row_step(typename Acc<T>::type (&acc)[kE], i
     }
 #pragma unroll
     for (int u = 0; u < kE; ++u) {
-        const int32_t kk = k + u * G;
+        const uint32_t kk = k + (uint32_t)(u * G);
         if (kk < k1) {
             Ac &a = one_chain ? acc[0] : acc[u];
             a = fma_acc(widen(val[u]), widen(ld_cached(x + col[u])), a);
@@ -204,8 +204,8 @@ bin_spmv_kernel(T *__restrict__ y, const int32_t *__restrict__ rp, const int32_t
         int32_t row = 0;
         if (valid) {
             row = __ldg(perm + pos);
-            const int32_t k1 = __ldg(rp + row + 1);
-            for (int32_t k = __ldg(rp + row) + lg; k < k1; k += G * kE)
+            const uint32_t k1 = (uint32_t)__ldg(rp + row + 1);
+            for (uint32_t k = (uint32_t)__ldg(rp + row) + (uint32_t)lg; k < k1; k += (uint32_t)(G * kE))
                 bin_row_step<T>(acc, k, k1, G, ci, vals, x);
         }
         if constexpr (sizeof(Ac) != 8) {

@@ -99,6 +99,41 @@ def test_gemv_beyond_2_31_entries(layout):
     torch.cuda.empty_cache()
 
 
+def test_csr_entries_near_2_31():
+    """58M rows with 5..64 random columns (about 2.0e9 stored entries, the top
+    of the int32 index range): the CSR product (warp-segmented kernel), the
+    row-binned product and the sparse inner product, checked at sampled rows
+    (the last rows hold entries just below 2^31) and by a closed form."""
+    from paper_1409_0669_gb300.csr_bin import BinnedCsr
+    m_rows = 58_000_000
+    rp, ci, v = synth.device_csr_block_(m_rows, 10, 5, 64, torch.float32, "cuda")
+    nnz = int(rp[-1].item())
+    assert 1_900_000_000 < nnz < 2 ** 31 - 1
+    x = synth.device_uniform_(torch.empty(m_rows, device="cuda"), 11)
+    lk = lak()
+    y = lk.csr_spmv(rp, ci, v, x)
+    yb = BinnedCsr(rp, ci, v, m_rows).spmv(x)
+    torch.cuda.synchronize()
+    xh = x.cpu()
+    g = synth.rng(12)
+    rows = sorted(set([0, m_rows - 2, m_rows - 1] + list(g.integers(0, m_rows, 25))))
+    rph = rp[torch.tensor(rows + [r + 1 for r in rows], device="cuda")].cpu().numpy()
+    for t, r in enumerate(rows):
+        a, b = int(rph[t]), int(rph[len(rows) + t])
+        vr, cr = v[a:b].cpu(), ci[a:b].cpu()
+        ref = oracle.sparse_dot(vr, cr, xh)
+        bound = 1e-5 * float(np.abs(host(vr)) @ np.abs(host(xh)[cr.numpy()]))
+        assert abs(float(y[r]) - ref) <= bound, (r, float(y[r]), ref)
+        assert abs(float(yb[r]) - ref) <= bound, (r, float(yb[r]), ref)
+    del y, yb
+    # sum over all stored entries of 1 * 1 = nnz, rounded once to the FP32 output
+    ones_v = torch.ones_like(v)
+    s = lk.vec_dot_sparse(ones_v, ci, torch.ones_like(x)).item()
+    assert s == float(np.float32(nnz))
+    del rp, ci, v, x, ones_v
+    torch.cuda.empty_cache()
+
+
 def test_csr_rejects_nnz_at_2_31():
     from paper_1409_0669_gb300 import _native
     lib = _native.load()
