@@ -112,6 +112,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 axpy_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                   const AxpyItem *__restrict__ items) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
     const UnitRange ur = unit_range(total, head->inc);
@@ -148,6 +149,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                  const DotItem *__restrict__ items, unsigned int *tickets, double *partials) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     __shared__ double wsum[32];
     const int64_t count = head->count, total = head->total_units, ue = head->unit_elems;
@@ -221,6 +223,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(kGemvBatchMaxBlock, 8)
 gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                   const GemvItem *__restrict__ items) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     const int64_t count = head->count, total = head->total_units;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -258,6 +261,7 @@ template <typename T, int U>
 __global__ void __launch_bounds__(512)
 spmv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__ offs,
                   const CsrItem *__restrict__ items) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     __shared__ int64_t rs_all[16][33];
     __shared__ Ac racc_all[16][32];
@@ -298,11 +302,11 @@ lak_status run_typed(const lak_batch_info &info, const char *table, void *ws, di
     const int vec = info.cfg.vec;
 #define LAK_VECSW(KERNEL, ...)                                                              \
     switch (vec) {                                                                          \
-    case 1: KERNEL<T, 1><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
-    case 2: KERNEL<T, 2><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
-    case 4: KERNEL<T, 4><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
-    case 8: KERNEL<T, 8><<<grid, block, 0, s>>>(__VA_ARGS__); break;                        \
-    case 16: KERNEL<T, 16><<<grid, block, 0, s>>>(__VA_ARGS__); break;                      \
+    case 1: launch_k(KERNEL<T, 1>, grid, block, 0, s, __VA_ARGS__); break;                        \
+    case 2: launch_k(KERNEL<T, 2>, grid, block, 0, s, __VA_ARGS__); break;                        \
+    case 4: launch_k(KERNEL<T, 4>, grid, block, 0, s, __VA_ARGS__); break;                        \
+    case 8: launch_k(KERNEL<T, 8>, grid, block, 0, s, __VA_ARGS__); break;                        \
+    case 16: launch_k(KERNEL<T, 16>, grid, block, 0, s, __VA_ARGS__); break;                      \
     default: return fail(LAK_EINVAL, "lak_batch_run: unsupported vec %d", vec);             \
     }
     switch ((lak_op)info.op) {

@@ -35,6 +35,7 @@ __device__ __forceinline__ int row_bin(int64_t len) {
 
 __global__ void __launch_bounds__(kTile)
 bin_count_kernel(const int32_t *__restrict__ rp, int64_t m, int32_t *__restrict__ counts) {
+    LAK_PDL_ENTRY();
     __shared__ int32_t c[kNB];
     if (threadIdx.x < kNB) c[threadIdx.x] = 0;
     __syncthreads();
@@ -49,6 +50,7 @@ bin_count_kernel(const int32_t *__restrict__ rp, int64_t m, int32_t *__restrict_
 __global__ void __launch_bounds__(1024)
 bin_scan_kernel(const int32_t *__restrict__ counts, int64_t tiles, int32_t *__restrict__ offsets,
                 int64_t *__restrict__ bin_ptr) {
+    LAK_PDL_ENTRY();
     __shared__ int64_t total[kNB];
     __shared__ int64_t warp_sum[32];
     __shared__ int64_t carry;
@@ -118,6 +120,7 @@ bin_scan_kernel(const int32_t *__restrict__ counts, int64_t tiles, int32_t *__re
 __global__ void __launch_bounds__(kTile)
 bin_scatter_kernel(const int32_t *__restrict__ rp, int64_t m, const int32_t *__restrict__ offsets,
                    int32_t *__restrict__ perm) {
+    LAK_PDL_ENTRY();
     __shared__ int32_t wc[kTile / 32][kNB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kTile + threadIdx.x;
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(256, 8)
 bin_spmv_kernel(T *__restrict__ y, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                 const T *__restrict__ vals, const T *__restrict__ x,
                 const int32_t *__restrict__ perm, const int64_t *__restrict__ bin_ptr) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     __shared__ int32_t sb[kNB + 1];
     __shared__ int32_t wpre[kNB + 1];     // first warp task of every bin
@@ -262,9 +266,9 @@ LAK_API lak_status csr_bin_build(int32_t *perm, int64_t *bin_ptr, const int32_t 
     if (tiles > 0x7fffffffLL) return fail(LAK_EINVAL, "csr_bin_build: too many rows");
     int32_t *counts = static_cast<int32_t *>(workspace);
     int32_t *offsets = counts + tiles * kNB;
-    bin_count_kernel<<<(unsigned)tiles, kTile, 0, s>>>(row_ptr, m, counts);
-    bin_scan_kernel<<<1, 1024, 0, s>>>(counts, tiles, offsets, bin_ptr);
-    bin_scatter_kernel<<<(unsigned)tiles, kTile, 0, s>>>(row_ptr, m, offsets, perm);
+    launch_k(bin_count_kernel, (unsigned)tiles, kTile, 0, s, row_ptr, m, counts);
+    launch_k(bin_scan_kernel, 1, 1024, 0, s, counts, tiles, offsets, bin_ptr);
+    launch_k(bin_scatter_kernel, (unsigned)tiles, kTile, 0, s, row_ptr, m, offsets, perm);
     return check_launch("csr_bin_build");
 }
 
@@ -299,7 +303,7 @@ LAK_API lak_status csr_bin_spmv(void *y, const int32_t *row_ptr, const int32_t *
                 return fail(LAK_ECUDA, "csr_bin_spmv: occupancy query failed");
             grid = per_sm * di->sms;
         }
-        kernel<<<grid, block, 0, s>>>(yp, row_ptr, col_idx, vp, xp, perm, bin_ptr);
+        launch_k(kernel, grid, block, 0, s, yp, row_ptr, col_idx, vp, xp, perm, bin_ptr);
         return check_launch("csr_bin_spmv");
     };
 #define LAK_BIN(T)                                                                               \

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(512)
 gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict__ x, int64_t m,
                 int64_t n, int64_t lda, int G, int inc, typename Acc<T>::type alpha,
                 typename Acc<T>::type beta) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     __shared__ Ac red[32];
     const int R = blockDim.x / G;                  // rows per block step
@@ -107,6 +108,7 @@ gemv_col_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
                 int64_t n, int64_t lda, int64_t cols_per_split,
                 typename Acc<T>::type *__restrict__ partials, unsigned int *__restrict__ tickets,
                 typename Acc<T>::type alpha, typename Acc<T>::type beta) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ac *red = reinterpret_cast<Ac *>(smem_raw);    // [nwarps][32*V]
@@ -187,7 +189,7 @@ lak_status gemv_row_t(void *y, const void *A, const void *x, int64_t m, int64_t 
     const T *Ap = static_cast<const T *>(A);
     const T *xp = static_cast<const T *>(x);
 #define LAK_ROW(VV) \
-    gemv_row_kernel<T, VV><<<L.grid, L.block, 0, s>>>(yp, Ap, xp, m, n, lda, G, L.inc, (Ac)alpha, \
+    launch_k(gemv_row_kernel<T, VV>, L.grid, L.block, 0, s, yp, Ap, xp, m, n, lda, G, L.inc, (Ac)alpha, \
                                                       (Ac)beta)
     switch (L.vec) {
     case 1: LAK_ROW(1); break;
@@ -226,7 +228,7 @@ lak_status gemv_col_t(void *y, const void *A, const void *x, int64_t m, int64_t 
                 return fail(LAK_ECUDA, "dense_gemv: shared memory %zu: %s", smem,             \
                             cudaGetErrorString(e));                                           \
         }                                                                                     \
-        gemv_col_kernel<T, VV><<<grid, L.block, smem, s>>>(yp, Ap, xp, m, n, lda, cps,        \
+        launch_k(gemv_col_kernel<T, VV>, grid, L.block, smem, s, yp, Ap, xp, m, n, lda, cps,        \
                                                            partials, tickets, (Ac)alpha,      \
                                                            (Ac)beta);                         \
     } while (0)

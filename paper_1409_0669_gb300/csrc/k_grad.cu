@@ -22,6 +22,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 outer_kernel(T *__restrict__ dA, const T *__restrict__ dy, const T *__restrict__ x, int64_t m,
              int64_t n, int64_t ldd, bool vec_ok) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     const int64_t rows_per = (m + gridDim.y - 1) / gridDim.y;
     const int64_t r0 = (int64_t)blockIdx.y * rows_per;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(512)
 sampled_outer_kernel(T *__restrict__ dvals, const int32_t *__restrict__ rp,
                      const int32_t *__restrict__ ci, const T *__restrict__ dy,
                      const T *__restrict__ x, int64_t m) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     const int lg = threadIdx.x % G;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
@@ -82,6 +84,7 @@ sampled_outer_kernel(T *__restrict__ dvals, const int32_t *__restrict__ rp,
 
 __global__ void count_cols_kernel(int32_t *__restrict__ counts, const int32_t *__restrict__ ci,
                                   int64_t nnz) {
+    LAK_PDL_ENTRY();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(counts + __ldg(ci + k), 1);      // integer: order-independent
@@ -94,6 +97,7 @@ constexpr int64_t kScanTile = (int64_t)kScanBlock * kScanPer;
 // Inclusive scan of v[0..len) in tiles; tile totals to sums[tile].
 __global__ void __launch_bounds__(kScanBlock)
 scan_tiles_kernel(int32_t *__restrict__ v, int64_t len, int32_t *__restrict__ sums) {
+    LAK_PDL_ENTRY();
     __shared__ int32_t warp_tot[kScanBlock / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     int32_t loc[kScanPer];
@@ -136,6 +140,7 @@ scan_tiles_kernel(int32_t *__restrict__ v, int64_t len, int32_t *__restrict__ su
 // Adds the inclusive prefix of earlier tiles' totals (sums already scanned).
 __global__ void add_tile_offsets_kernel(int32_t *__restrict__ v, int64_t len,
                                         const int32_t *__restrict__ sums_scanned) {
+    LAK_PDL_ENTRY();
     const int64_t tile = blockIdx.x;
     if (tile == 0) return;
     const int32_t off = sums_scanned[tile - 1];
@@ -146,6 +151,7 @@ __global__ void add_tile_offsets_kernel(int32_t *__restrict__ v, int64_t len,
 
 __global__ void copy_i32_kernel(int32_t *__restrict__ dst, const int32_t *__restrict__ src,
                                 int64_t len) {
+    LAK_PDL_ENTRY();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len;
          k += (int64_t)gridDim.x * blockDim.x)
         dst[k] = src[k];
@@ -154,6 +160,7 @@ __global__ void copy_i32_kernel(int32_t *__restrict__ dst, const int32_t *__rest
 __global__ void scatter_kernel(int32_t *__restrict__ row_idx, int32_t *__restrict__ perm,
                                int32_t *__restrict__ cursor, const int32_t *__restrict__ rp,
                                const int32_t *__restrict__ ci, int64_t m) {
+    LAK_PDL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k1 = rp[i + 1];
@@ -170,6 +177,7 @@ __global__ void scatter_kernel(int32_t *__restrict__ row_idx, int32_t *__restric
 // order in which the scatter's atomics were served.
 __global__ void sort_columns_kernel(int32_t *__restrict__ row_idx, int32_t *__restrict__ perm,
                                     const int32_t *__restrict__ cp, int64_t n) {
+    LAK_PDL_ENTRY();
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = cp[j], b = cp[j + 1];
@@ -192,6 +200,7 @@ __global__ void sort_columns_kernel(int32_t *__restrict__ row_idx, int32_t *__re
 template <typename E>
 __global__ void gather_kernel(E *__restrict__ dst, const E *__restrict__ src,
                               const int32_t *__restrict__ idx, int64_t n) {
+    LAK_PDL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = src[__ldg(idx + i)];
@@ -200,6 +209,7 @@ __global__ void gather_kernel(E *__restrict__ dst, const E *__restrict__ src,
 template <typename T, typename S>
 __global__ void scale_dev_kernel(T *__restrict__ out, const T *__restrict__ v,
                                  const S *__restrict__ alpha, int64_t n) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     const A a = static_cast<A>(*alpha);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -235,7 +245,7 @@ lak_status outer_t(void *dA, const void *dy, const void *x, int64_t m, int64_t n
     if (gy < 1) gy = 1;
     if (gy > m) gy = m;
     if (gy > 65535) gy = 65535;
-    outer_kernel<T, V><<<dim3((unsigned)gx, (unsigned)gy), block, 0, s>>>(
+    launch_k(outer_kernel<T, V>, dim3((unsigned)gx, (unsigned)gy), block, 0, s, 
         static_cast<T *>(dA), static_cast<const T *>(dy), static_cast<const T *>(x), m, n, ldd,
         vec_ok);
     return check_launch("dense_outer");
@@ -283,7 +293,7 @@ LAK_API lak_status csr_sampled_outer(void *dvals, const int32_t *row_ptr, const 
     const int G = mean <= 12 ? 1 : mean <= 16 ? 8 : mean <= 32 ? 16 : 32;
     const int grid = grid_for(m * G, block);
 #define LAK_SOG(T, GG)                                                                         \
-    sampled_outer_kernel<T, GG><<<grid, block, 0, s>>>(static_cast<T *>(dvals), row_ptr, col_idx, \
+    launch_k(sampled_outer_kernel<T, GG>, grid, block, 0, s, static_cast<T *>(dvals), row_ptr, col_idx, \
                                                        static_cast<const T *>(dy),              \
                                                        static_cast<const T *>(x), m)
 #define LAK_SO(T)                     \
@@ -344,20 +354,20 @@ LAK_API lak_status csr_transpose(int32_t *col_ptr, int32_t *row_idx, int32_t *pe
                     (long long)n);
     const int block = 256;
     // counts land in col_ptr[1..n]
-    count_cols_kernel<<<grid_for(nnz, block), block, 0, s>>>(col_ptr + 1, col_idx, nnz);
+    launch_k(count_cols_kernel, grid_for(nnz, block), block, 0, s, col_ptr + 1, col_idx, nnz);
     // inclusive scan of col_ptr[1..n] -> col_ptr[j+1] = entries in columns <= j
-    scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(col_ptr + 1, n, sums);
+    launch_k(scan_tiles_kernel, (unsigned)tiles, kScanBlock, 0, s, col_ptr + 1, n, sums);
     if (tiles > 1) {
-        scan_tiles_kernel<<<(unsigned)tiles2, kScanBlock, 0, s>>>(sums, tiles, sums2);
+        launch_k(scan_tiles_kernel, (unsigned)tiles2, kScanBlock, 0, s, sums, tiles, sums2);
         if (tiles2 > 1) {
-            scan_tiles_kernel<<<1, kScanBlock, 0, s>>>(sums2, tiles2, sums2 + tiles2);
-            add_tile_offsets_kernel<<<(unsigned)tiles2, 256, 0, s>>>(sums, tiles, sums2);
+            launch_k(scan_tiles_kernel, 1, kScanBlock, 0, s, sums2, tiles2, sums2 + tiles2);
+            launch_k(add_tile_offsets_kernel, (unsigned)tiles2, 256, 0, s, sums, tiles, sums2);
         }
-        add_tile_offsets_kernel<<<(unsigned)tiles, 256, 0, s>>>(col_ptr + 1, n, sums);
+        launch_k(add_tile_offsets_kernel, (unsigned)tiles, 256, 0, s, col_ptr + 1, n, sums);
     }
-    copy_i32_kernel<<<grid_for(n, block), block, 0, s>>>(cursor, col_ptr, n);
-    scatter_kernel<<<grid_for(m, block), block, 0, s>>>(row_idx, perm, cursor, row_ptr, col_idx, m);
-    sort_columns_kernel<<<grid_for(n, block), block, 0, s>>>(row_idx, perm, col_ptr, n);
+    launch_k(copy_i32_kernel, grid_for(n, block), block, 0, s, cursor, col_ptr, n);
+    launch_k(scatter_kernel, grid_for(m, block), block, 0, s, row_idx, perm, cursor, row_ptr, col_idx, m);
+    launch_k(sort_columns_kernel, grid_for(n, block), block, 0, s, row_idx, perm, col_ptr, n);
     return check_launch("csr_transpose");
 }
 
@@ -371,9 +381,9 @@ LAK_API lak_status vec_gather(void *dst, const void *src, const int32_t *idx, in
     const int block = 256;
     const int grid = grid_for(n, block);
     switch (esize(dtype)) {
-    case 2: gather_kernel<uint16_t><<<grid, block, 0, s>>>((uint16_t *)dst, (const uint16_t *)src, idx, n); break;
-    case 4: gather_kernel<uint32_t><<<grid, block, 0, s>>>((uint32_t *)dst, (const uint32_t *)src, idx, n); break;
-    case 8: gather_kernel<uint64_t><<<grid, block, 0, s>>>((uint64_t *)dst, (const uint64_t *)src, idx, n); break;
+    case 2: launch_k(gather_kernel<uint16_t>, grid, block, 0, s, (uint16_t *)dst, (const uint16_t *)src, idx, n); break;
+    case 4: launch_k(gather_kernel<uint32_t>, grid, block, 0, s, (uint32_t *)dst, (const uint32_t *)src, idx, n); break;
+    case 8: launch_k(gather_kernel<uint64_t>, grid, block, 0, s, (uint64_t *)dst, (const uint64_t *)src, idx, n); break;
     }
     return check_launch("vec_gather");
 }
@@ -388,10 +398,10 @@ LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, in
     const int block = 256;
     const int grid = grid_for(n, block);
     switch (dtype) {
-    case LAK_F32: scale_dev_kernel<float, float><<<grid, block, 0, s>>>((float *)out, (const float *)v, (const float *)alpha, n); break;
-    case LAK_F64: scale_dev_kernel<double, double><<<grid, block, 0, s>>>((double *)out, (const double *)v, (const double *)alpha, n); break;
-    case LAK_BF16: scale_dev_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>((__nv_bfloat16 *)out, (const __nv_bfloat16 *)v, (const float *)alpha, n); break;
-    case LAK_F16: scale_dev_kernel<__half, float><<<grid, block, 0, s>>>((__half *)out, (const __half *)v, (const float *)alpha, n); break;
+    case LAK_F32: launch_k(scale_dev_kernel<float, float>, grid, block, 0, s, (float *)out, (const float *)v, (const float *)alpha, n); break;
+    case LAK_F64: launch_k(scale_dev_kernel<double, double>, grid, block, 0, s, (double *)out, (const double *)v, (const double *)alpha, n); break;
+    case LAK_BF16: launch_k(scale_dev_kernel<__nv_bfloat16, float>, grid, block, 0, s, (__nv_bfloat16 *)out, (const __nv_bfloat16 *)v, (const float *)alpha, n); break;
+    case LAK_F16: launch_k(scale_dev_kernel<__half, float>, grid, block, 0, s, (__half *)out, (const __half *)v, (const float *)alpha, n); break;
     }
     return check_launch("vec_scale_dev");
 }

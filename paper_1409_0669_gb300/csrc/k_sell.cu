@@ -22,6 +22,7 @@ constexpr int kC = 32;
 constexpr int kMaxSigma = 4096;
 
 __global__ void identity_perm_kernel(int32_t *perm, int64_t m, int64_t mp) {
+    LAK_PDL_ENTRY();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < mp;
          p += (int64_t)gridDim.x * blockDim.x)
         perm[p] = p < m ? (int32_t)p : -1;
@@ -30,6 +31,7 @@ __global__ void identity_perm_kernel(int32_t *perm, int64_t m, int64_t mp) {
 // One block per window: rank each row by (length desc, index asc).
 __global__ void window_sort_kernel(int32_t *perm, const int32_t *__restrict__ rp, int64_t m,
                                    int64_t mp, int sigma) {
+    LAK_PDL_ENTRY();
     extern __shared__ int32_t lens[];
     const int64_t w0 = (int64_t)blockIdx.x * sigma;
     const int wn = (int)(mp - w0 < sigma ? mp - w0 : sigma);
@@ -53,6 +55,7 @@ __global__ void window_sort_kernel(int32_t *perm, const int32_t *__restrict__ rp
 // One warp per slice: the longest row of the slice.
 __global__ void slice_len_kernel(int32_t *slen, const int32_t *__restrict__ perm,
                                  const int32_t *__restrict__ rp, int64_t ns) {
+    LAK_PDL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -71,6 +74,7 @@ __global__ void slice_len_kernel(int32_t *slen, const int32_t *__restrict__ perm
 // Single block: slice_ptr = exclusive prefix of 32 * slice_len; slice_ptr[ns] = total.
 __global__ void __launch_bounds__(1024)
 slice_ptr_kernel(int64_t *sptr, const int32_t *__restrict__ slen, int64_t ns) {
+    LAK_PDL_ENTRY();
     __shared__ int64_t part[1024];
     const int T = blockDim.x;
     const int64_t per = (ns + T - 1) / T;
@@ -98,6 +102,7 @@ __global__ void fill_kernel(int32_t *cols, int32_t *map, const int32_t *__restri
                             const int32_t *__restrict__ ci, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ slen, const int64_t *__restrict__ sptr,
                             int64_t mp) {
+    LAK_PDL_ENTRY();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < mp;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = p / kC;
@@ -123,6 +128,7 @@ __global__ void fill_kernel(int32_t *cols, int32_t *map, const int32_t *__restri
 template <typename E>
 __global__ void pack_kernel(E *__restrict__ dst, const E *__restrict__ src,
                             const int32_t *__restrict__ map, int64_t total) {
+    LAK_PDL_ENTRY();
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = map[q];
@@ -136,6 +142,7 @@ sell_spmv_kernel(T *__restrict__ y, const int64_t *__restrict__ sptr,
                  const int32_t *__restrict__ slen, const int32_t *__restrict__ perm,
                  const int32_t *__restrict__ cols, const T *__restrict__ vals,
                  const T *__restrict__ x, int64_t ns, int inc) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
@@ -200,7 +207,7 @@ lak_status sell_spmv_t(void *y, const int64_t *sptr, const int32_t *slen, const 
     int64_t grid = c.grid > 0 ? c.grid : (ns + wpb - 1) / wpb;
     if (grid > 0x7fffffff) grid = 0x7fffffff;
 #define LAK_SELL(UU) \
-    sell_spmv_kernel<T, UU><<<(unsigned)grid, c.block, 0, s>>>(yp, sptr, slen, perm, cols, vp, xp, \
+    launch_k(sell_spmv_kernel<T, UU>, (unsigned)grid, c.block, 0, s, yp, sptr, slen, perm, cols, vp, xp, \
                                                                 ns, c.increment)
     switch (c.vec) {
     case 1: LAK_SELL(1); break;
@@ -243,12 +250,12 @@ LAK_API lak_status csr_to_sell_count(const int32_t *row_ptr, int64_t m, int32_t 
     if (!row_ptr || !perm || !slice_len) return fail(LAK_EINVAL, "csr_to_sell_count: NULL pointer");
     const int block = 256;
     if (sigma == 1)
-        identity_perm_kernel<<<grid_for(mp, block), block, 0, s>>>(perm, m, mp);
+        launch_k(identity_perm_kernel, grid_for(mp, block), block, 0, s, perm, m, mp);
     else
-        window_sort_kernel<<<(unsigned)((mp + sigma - 1) / sigma), 256, sigma * 4, s>>>(
+        launch_k(window_sort_kernel, (unsigned)((mp + sigma - 1) / sigma), 256, sigma * 4, s, 
             perm, row_ptr, m, mp, sigma);
-    slice_len_kernel<<<grid_for(ns * 32, block), block, 0, s>>>(slice_len, perm, row_ptr, ns);
-    slice_ptr_kernel<<<1, 1024, 0, s>>>(slice_ptr, slice_len, ns);
+    launch_k(slice_len_kernel, grid_for(ns * 32, block), block, 0, s, slice_len, perm, row_ptr, ns);
+    launch_k(slice_ptr_kernel, 1, 1024, 0, s, slice_ptr, slice_len, ns);
     return check_launch("csr_to_sell_count");
 }
 
@@ -262,7 +269,7 @@ LAK_API lak_status csr_to_sell_fill(const int32_t *row_ptr, const int32_t *col_i
         return fail(LAK_EINVAL, "csr_to_sell_fill: NULL pointer");
     const int64_t mp = (m + kC - 1) / kC * kC;
     const int block = 256;
-    fill_kernel<<<grid_for(mp, block), block, 0, (cudaStream_t)stream>>>(
+    launch_k(fill_kernel, grid_for(mp, block), block, 0, (cudaStream_t)stream, 
         cols, map, row_ptr, col_idx, perm, slice_len, slice_ptr, mp);
     return check_launch("csr_to_sell_fill");
 }
@@ -277,9 +284,9 @@ LAK_API lak_status sell_pack_values(void *sell_vals, const void *csr_vals, const
     const int grid = grid_for(total, block);
     cudaStream_t s = (cudaStream_t)stream;
     switch (esize(dtype)) {
-    case 2: pack_kernel<uint16_t><<<grid, block, 0, s>>>((uint16_t *)sell_vals, (const uint16_t *)csr_vals, map, total); break;
-    case 4: pack_kernel<uint32_t><<<grid, block, 0, s>>>((uint32_t *)sell_vals, (const uint32_t *)csr_vals, map, total); break;
-    case 8: pack_kernel<uint64_t><<<grid, block, 0, s>>>((uint64_t *)sell_vals, (const uint64_t *)csr_vals, map, total); break;
+    case 2: launch_k(pack_kernel<uint16_t>, grid, block, 0, s, (uint16_t *)sell_vals, (const uint16_t *)csr_vals, map, total); break;
+    case 4: launch_k(pack_kernel<uint32_t>, grid, block, 0, s, (uint32_t *)sell_vals, (const uint32_t *)csr_vals, map, total); break;
+    case 8: launch_k(pack_kernel<uint64_t>, grid, block, 0, s, (uint64_t *)sell_vals, (const uint64_t *)csr_vals, map, total); break;
     }
     return check_launch("sell_pack_values");
 }

@@ -30,6 +30,7 @@ template <typename T, int U, int P>
 __global__ void __launch_bounds__(512)
 spmv_kernel(T *__restrict__ y, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const T *__restrict__ vals, const T *__restrict__ x, int64_t m, int G, int inc) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     const int R = blockDim.x / G;
     const int grp = threadIdx.x / G;
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(512)
 spmv_seg_kernel(T *__restrict__ y, const int32_t *__restrict__ rp,
                 const int32_t *__restrict__ ci, const T *__restrict__ vals,
                 const T *__restrict__ x, int64_t m, int inc) {
+    LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
     __shared__ int64_t rs_all[16][33];
     __shared__ Ac racc_all[16][32];
@@ -127,11 +129,11 @@ lak_status spmv_seg_launch(T *yp, const int32_t *rp, const int32_t *ci, const T 
     const bool vload = U % 4 == 0 && (uintptr_t)ci % 16 == 0 && (uintptr_t)vp % 16 == 0;
     if constexpr (U % 4 == 0) {
         if (vload) {
-            spmv_seg_kernel<T, U, true><<<L.grid, L.block, 0, s>>>(yp, rp, ci, vp, xp, m, L.inc);
+            launch_k(spmv_seg_kernel<T, U, true>, L.grid, L.block, 0, s, yp, rp, ci, vp, xp, m, L.inc);
             return check_launch("csr_spmv (warp-segmented)");
         }
     }
-    spmv_seg_kernel<T, U, false><<<L.grid, L.block, 0, s>>>(yp, rp, ci, vp, xp, m, L.inc);
+    launch_k(spmv_seg_kernel<T, U, false>, L.grid, L.block, 0, s, yp, rp, ci, vp, xp, m, L.inc);
     return check_launch("csr_spmv (warp-segmented)");
 }
 
@@ -154,10 +156,10 @@ lak_status spmv_t(void *y, const int32_t *rp, const int32_t *ci, const void *val
 #define LAK_SPMV(UU)                                                                      \
     do {                                                                                  \
         if (G <= 4)                                                                       \
-            spmv_kernel<T, UU, CACHED><<<L.grid, L.block, 0, s>>>(yp, rp, ci, vp, xp, m, G, \
+            launch_k(spmv_kernel<T, UU, CACHED>, L.grid, L.block, 0, s, yp, rp, ci, vp, xp, m, G, \
                                                                   L.inc);                 \
         else                                                                              \
-            spmv_kernel<T, UU, STREAM><<<L.grid, L.block, 0, s>>>(yp, rp, ci, vp, xp, m, G, \
+            launch_k(spmv_kernel<T, UU, STREAM>, L.grid, L.block, 0, s, yp, rp, ci, vp, xp, m, G, \
                                                                   L.inc);                 \
     } while (0)
     switch (L.vec) {

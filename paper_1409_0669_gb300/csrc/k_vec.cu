@@ -17,6 +17,7 @@ template <typename E, int V>
 __global__ void __launch_bounds__(512)
 copy_kernel(E *__restrict__ x, const E *__restrict__ y, int64_t n, int64_t head,
             int64_t nchunks, int inc) {
+    LAK_PDL_ENTRY();
     const E *yb = y + head;
     E *xb = x + head;
     const Range r = chunk_range(nchunks, inc);
@@ -40,6 +41,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 axpy_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, int64_t n, int64_t head,
             int64_t nchunks, int inc) {
+    LAK_PDL_ENTRY();
     // x may alias y or z, so the loads take the coherent path
     const Range r = chunk_range(nchunks, inc);
     for (int64_t c = r.begin; c < r.end; c += r.stride) {
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(512)
 dot_kernel(void *out, const T *__restrict__ x, const T *__restrict__ y, int64_t n,
            int64_t head, int64_t nchunks, int inc, unsigned int *counter,
            double *partials) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     A acc[V];
 #pragma unroll
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(512)
 dot_comp_kernel(double *out, const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                 int64_t head, int64_t nchunks, int inc, unsigned int *counter,
                 double *partials) {
+    LAK_PDL_ENTRY();
     float sv[V], cv[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) sv[v] = cv[v] = 0.0f;
@@ -172,11 +176,11 @@ lak_status copy_vec(int vec, E *x, const E *y, int64_t n, int64_t head, const La
                     cudaStream_t s) {
     const int64_t nchunks = (n - head) / vec;
     switch (vec) {
-    case 1: copy_kernel<E, 1><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
-    case 2: copy_kernel<E, 2><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
-    case 4: copy_kernel<E, 4><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
-    case 8: copy_kernel<E, 8><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
-    case 16: copy_kernel<E, 16><<<L.grid, L.block, 0, s>>>(x, y, n, head, nchunks, L.inc); break;
+    case 1: launch_k(copy_kernel<E, 1>, L.grid, L.block, 0, s, x, y, n, head, nchunks, L.inc); break;
+    case 2: launch_k(copy_kernel<E, 2>, L.grid, L.block, 0, s, x, y, n, head, nchunks, L.inc); break;
+    case 4: launch_k(copy_kernel<E, 4>, L.grid, L.block, 0, s, x, y, n, head, nchunks, L.inc); break;
+    case 8: launch_k(copy_kernel<E, 8>, L.grid, L.block, 0, s, x, y, n, head, nchunks, L.inc); break;
+    case 16: launch_k(copy_kernel<E, 16>, L.grid, L.block, 0, s, x, y, n, head, nchunks, L.inc); break;
     default: return fail(LAK_EINVAL, "vec_copy: unsupported vec %d", vec);
     }
     return check_launch("vec_copy");
@@ -192,11 +196,11 @@ lak_status axpy_t(int vec, void *x, const void *y, const void *z, double alpha, 
     const A a = static_cast<A>(alpha);
     const int64_t nchunks = (n - head) / vec;
     switch (vec) {
-    case 1: axpy_kernel<T, 1><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
-    case 2: axpy_kernel<T, 2><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
-    case 4: axpy_kernel<T, 4><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
-    case 8: axpy_kernel<T, 8><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
-    case 16: axpy_kernel<T, 16><<<L.grid, L.block, 0, s>>>(xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 1: launch_k(axpy_kernel<T, 1>, L.grid, L.block, 0, s, xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 2: launch_k(axpy_kernel<T, 2>, L.grid, L.block, 0, s, xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 4: launch_k(axpy_kernel<T, 4>, L.grid, L.block, 0, s, xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 8: launch_k(axpy_kernel<T, 8>, L.grid, L.block, 0, s, xp, yp, zp, a, n, head, nchunks, L.inc); break;
+    case 16: launch_k(axpy_kernel<T, 16>, L.grid, L.block, 0, s, xp, yp, zp, a, n, head, nchunks, L.inc); break;
     default: return fail(LAK_EINVAL, "vec_axpy: unsupported vec %d", vec);
     }
     return check_launch("vec_axpy");
@@ -211,7 +215,7 @@ lak_status dot_t(int vec, void *out, const void *x, const void *y, int64_t n, in
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const int64_t nchunks = (n - head) / vec;
 #define LAK_DOT(VV)                                                                     \
-    dot_kernel<T, VV><<<L.grid, L.block, 0, s>>>(out, xp, yp, n, head, nchunks, L.inc, \
+    launch_k(dot_kernel<T, VV>, L.grid, L.block, 0, s, out, xp, yp, n, head, nchunks, L.inc, \
                                                  counter, partials)
     switch (vec) {
     case 1: LAK_DOT(1); break;
@@ -235,7 +239,7 @@ lak_status dot_comp_t(int vec, void *out, const void *x, const void *y, int64_t 
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const int64_t nchunks = (n - head) / vec;
 #define LAK_DOTC(VV)                                                                    \
-    dot_comp_kernel<T, VV><<<L.grid, L.block, 0, s>>>(o, xp, yp, n, head, nchunks, L.inc, \
+    launch_k(dot_comp_kernel<T, VV>, L.grid, L.block, 0, s, o, xp, yp, n, head, nchunks, L.inc, \
                                                       counter, partials)
     switch (vec) {
     case 1: LAK_DOTC(1); break;

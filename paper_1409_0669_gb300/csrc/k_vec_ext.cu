@@ -18,6 +18,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(512)
 axpby_kernel(T *x, typename Acc<T>::type alpha, const T *y, typename Acc<T>::type beta,
              const T *z, int64_t n, int64_t head, int64_t nchunks, int inc) {
+    LAK_PDL_ENTRY();
     const Range r = chunk_range(nchunks, inc);
     for (int64_t c = r.begin; c < r.end; c += r.stride) {
         const int64_t o = head + c * V;
@@ -42,6 +43,7 @@ template <typename T>
 __global__ void __launch_bounds__(512)
 axpby_strided_kernel(T *x, int64_t incx, typename Acc<T>::type alpha, const T *y, int64_t incy,
                      typename Acc<T>::type beta, const T *z, int64_t incz, int64_t n) {
+    LAK_PDL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         x[i * incx] = narrow<T>(fma_acc(alpha, widen(y[i * incy]), beta * widen(z[i * incz])));
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(512, 2)     // two 512-thread blocks per SM
 axpy_norm2_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, void *out,
                   int64_t n, int64_t head, int64_t nchunks, int inc, unsigned int *counter,
                   double *partials) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     A acc[V];
 #pragma unroll
@@ -103,6 +106,7 @@ __global__ void __launch_bounds__(512)
 dot_sparse_kernel(void *out, const T *__restrict__ vals, const int32_t *__restrict__ idx,
                   const T *__restrict__ y, int64_t nnz, int64_t head, int64_t nchunks, int inc,
                   unsigned int *counter, double *partials) {
+    LAK_PDL_ENTRY();
     using A = typename Acc<T>::type;
     A acc[V];
 #pragma unroll
@@ -147,7 +151,7 @@ lak_status dot_sparse_t(void *out, const void *vals, const int32_t *idx, const v
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const int64_t nchunks = (nnz - head) / L.vec;
 #define LAK_SD(VV)                                                                        \
-    dot_sparse_kernel<T, VV><<<L.grid, L.block, 0, s>>>(out, vp, idx, yp, nnz, head,       \
+    launch_k(dot_sparse_kernel<T, VV>, L.grid, L.block, 0, s, out, vp, idx, yp, nnz, head,       \
                                                         nchunks, L.inc, counter, partials)
     switch (L.vec) {
     case 1: LAK_SD(1); break;
@@ -169,7 +173,7 @@ lak_status axpby_t(void *x, double alpha, const void *y, double beta, const void
     const T *zp = static_cast<const T *>(z);
     const int64_t nchunks = (n - head) / L.vec;
 #define LAK_AB(VV)                                                                        \
-    axpby_kernel<T, VV><<<L.grid, L.block, 0, s>>>(xp, (A)alpha, yp, (A)beta, zp, n, head, \
+    launch_k(axpby_kernel<T, VV>, L.grid, L.block, 0, s, xp, (A)alpha, yp, (A)beta, zp, n, head, \
                                                    nchunks, L.inc)
     switch (L.vec) {
     case 1: LAK_AB(1); break;
@@ -188,7 +192,7 @@ lak_status axpby_strided_t(void *x, int64_t incx, double alpha, const void *y, i
                            double beta, const void *z, int64_t incz, int64_t n, int grid,
                            int block, cudaStream_t s) {
     using A = typename Acc<T>::type;
-    axpby_strided_kernel<T><<<grid, block, 0, s>>>(static_cast<T *>(x), incx, (A)alpha,
+    launch_k(axpby_strided_kernel<T>, grid, block, 0, s, static_cast<T *>(x), incx, (A)alpha,
                                                    static_cast<const T *>(y), incy, (A)beta,
                                                    static_cast<const T *>(z), incz, n);
     return check_launch("vec_axpby_strided");
@@ -205,7 +209,7 @@ lak_status axpy_norm2_t(void *x, const void *y, const void *z, double alpha, voi
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + LAK_WS_COUNTER_BYTES);
     const int64_t nchunks = (n - head) / L.vec;
 #define LAK_AN(VV)                                                                          \
-    axpy_norm2_kernel<T, VV><<<L.grid, L.block, 0, s>>>(xp, yp, zp, (A)alpha, out, n, head,   \
+    launch_k(axpy_norm2_kernel<T, VV>, L.grid, L.block, 0, s, xp, yp, zp, (A)alpha, out, n, head,   \
                                                         nchunks, L.inc, counter, partials)
     switch (L.vec) {
     case 1: LAK_AN(1); break;

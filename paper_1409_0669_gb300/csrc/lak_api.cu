@@ -42,6 +42,14 @@ bool g_dev_ok[kMaxDevices];
 std::mutex g_dev_mu;
 }  // namespace
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("LAK_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 const DeviceInfo *device_info() {
     int d = 0;
     cudaError_t e = cudaGetDevice(&d);

@@ -61,6 +61,40 @@ inline int access_bytes(int vec, int es) {
     return b > 32 ? 32 : b;
 }
 
+// Programmatic dependent launch (sm_90 and later).  Every kernel of the library
+// begins with LAK_PDL_ENTRY(): it waits until the kernel before it in the stream
+// has completed and its writes are visible (griddepcontrol.wait; a no-op when
+// the launch did not ask for programmatic serialization), then lets the next
+// kernel in the stream start launching (griddepcontrol.launch_dependents: the
+// next grid is scheduled once every block of this one has started, so its
+// launch and block set-up overlap this grid's tail instead of following it).
+// No kernel touches global memory before the wait, so the stream's ordering is
+// unchanged; launch_k launches with the attribute unless LAK_PDL=0.
+#define LAK_PDL_ENTRY()                                              \
+    do {                                                             \
+        asm volatile("griddepcontrol.wait;" ::: "memory");           \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+    } while (0)
+
+// Host: whether launches ask for programmatic serialization (LAK_PDL, read once).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // The configuration a batched launch starts from (explicit cfg, else the
 // batched kernels' own defaults), with vec filled in; host only, no CUDA
 // call; grid left as given.
