@@ -263,7 +263,7 @@ spmv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
                   const CsrItem *__restrict__ items) {
     LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
-    __shared__ int64_t rs_all[16][33];
+    __shared__ uint32_t rs_all[16][33];
     __shared__ Ac racc_all[16][32];
     const int64_t count = head->count, total = head->total_units;
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;

@@ -100,7 +100,7 @@ spmv_seg_kernel(T *__restrict__ y, const int32_t *__restrict__ rp,
                 const T *__restrict__ x, int64_t m, int inc) {
     LAK_PDL_ENTRY();
     using Ac = typename Acc<T>::type;
-    __shared__ int64_t rs_all[16][33];
+    __shared__ uint32_t rs_all[16][33];
     __shared__ Ac racc_all[16][32];
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;

@@ -155,10 +155,12 @@ constexpr DefaultCfg kDefaults[LAK_OP_COUNT][2][LAK_SIZE_BUCKETS] = {
 
 // CSR SpMV, warp-segmented kernel (mean row length 13..64): tuned on the
 // power-law matrix (2M rows), where the group-per-row entries above lose 6 %
-// (FP32) and 4 % (FP64).
+// (FP32) and 4 % (FP64).  FP64 takes 4 entries per lane: at 54 registers a
+// thread that leaves more warps resident than 8 entries (60 registers), and
+// the gathers, not the FP64 pipe, bound this kernel now (186 vs 195 us).
 constexpr DefaultCfg kSpmvSegDefaults[2][LAK_SIZE_BUCKETS] = {
     {{128, 0, 4, G_}, {128, 0, 4, G_}, {128, 0, 4, G_}, {128, 0, 4, G_}},
-    {{64, 0, 8, G_}, {64, 0, 8, G_}, {64, 0, 8, G_}, {64, 0, 8, G_}},
+    {{64, 0, 4, G_}, {64, 0, 4, G_}, {64, 0, 4, G_}, {64, 0, 4, G_}},
 };
 
 bool is_vector_op(lak_op op) { return op == LAK_OP_COPY || op == LAK_OP_AXPY || op == LAK_OP_DOT; }

@@ -6,10 +6,17 @@
 // current chunk, reads them with 16-byte vector loads when the arrays allow it,
 // and accumulates with one FMA per entry, closing a partial sum whenever it
 // crosses a row boundary.  A row that continues across lanes is joined by a
-// segmented inclusive scan over the lanes (5 shuffle steps); a row that
-// continues across chunks is joined in the warp's shared-memory accumulator.
-// Every (row, chunk) partial has exactly one writer, so the result is
-// deterministic and needs no atomics.  All 32 lanes of the warp must call it.
+// segmented inclusive scan over the lanes, with only as many shuffle steps as
+// the chunk's longest run of lanes needs (at most 5); a row that continues
+// across chunks leaves its running sum in the warp's shared-memory slot, and
+// lane 0 of the next chunk starts its FMA chain from it.  Every slot is only
+// ever stored (a row's running total, by the one lane that holds its last entry
+// in the chunk), so the result is deterministic and needs no atomics.
+//
+// Floating-point instructions per chunk: U FMAs per lane, one add per scan step
+// and one add to join the carried-in sum; a row that begins and ends inside a
+// lane costs no add at all.  This matters for FP64 on GB300, where the FP64
+// pipe, not memory, bounds the kernel.  All 32 lanes of the warp must call it.
 #pragma once
 
 #include "lak_internal.cuh"
@@ -20,29 +27,31 @@ template <typename T, int U, bool VLOAD>
 __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__restrict__ rp,
                                            const int32_t *__restrict__ ci,
                                            const T *__restrict__ vals, const T *__restrict__ x,
-                                           int64_t m, int64_t nnz, int64_t b, int64_t *rs,
+                                           int64_t m, int64_t nnz64, int64_t b, uint32_t *rs,
                                            typename Acc<T>::type *racc) {
     using Ac = typename Acc<T>::type;
-    constexpr int CH = 32 * U;
+    constexpr uint32_t CH = 32 * U;
+    // Entry positions fit in 32 bits: row_ptr is int32, so nnz < 2^31, and a
+    // position never exceeds nnz + CH < 2^32.
+    const uint32_t nnz = (uint32_t)nnz64;
     const int lane = threadIdx.x & 31;
     const int64_t row = b * 32 + lane;
-    const int64_t s_l = row < m ? (int64_t)__ldg(rp + row) : nnz;
-    rs[lane] = s_l;
-    if (lane == 31) rs[32] = (b * 32 + 32 < m) ? (int64_t)__ldg(rp + b * 32 + 32) : nnz;
+    rs[lane] = row < m ? (uint32_t)__ldg(rp + row) : nnz;
+    if (lane == 31) rs[32] = (b * 32 + 32 < m) ? (uint32_t)__ldg(rp + b * 32 + 32) : nnz;
     racc[lane] = Ac(0);
     __syncwarp();
-    const int64_t S = rs[0];
-    const int64_t E = rs[32];
-    const int64_t cbeg = VLOAD ? (S & ~(int64_t)3) : S;
-    for (int64_t c0 = cbeg; c0 < E; c0 += CH) {  // warp-uniform trip count
-        const int64_t k0 = c0 + (int64_t)lane * U;
+    const uint32_t S = rs[0];
+    const uint32_t E = rs[32];
+    const uint32_t cbeg = VLOAD ? (S & ~3u) : S;
+    for (uint32_t c0 = cbeg; c0 < E; c0 += CH) {  // warp-uniform trip count
+        const uint32_t k0 = c0 + (uint32_t)lane * U;
         int32_t col[U];
         T val[U];
         if constexpr (VLOAD) {
 #pragma unroll
             for (int q = 0; q < U; q += 4) {
-                const int64_t kq = k0 + q;
-                if (kq >= 0 && kq + 4 <= nnz) {
+                const uint32_t kq = k0 + q;
+                if (kq + 4 <= nnz) {
                     ld_raw<16, CACHED>(&col[q], ci + kq);
                     if constexpr (sizeof(T) == 8) {
                         ld_raw<16, CACHED>(&val[q], vals + kq);
@@ -55,7 +64,7 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
                 } else {
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int64_t k = kq + t;
+                        const uint32_t k = kq + t;
                         if (k >= S && k < E) {
                             col[q + t] = __ldg(ci + k);
                             val[q + t] = vals[k];
@@ -66,7 +75,7 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
         } else {
 #pragma unroll
             for (int j = 0; j < U; ++j) {
-                const int64_t k = k0 + j;
+                const uint32_t k = k0 + j;
                 if (k >= S && k < E) {
                     col[j] = __ldg(ci + k);
                     val[j] = vals[k];
@@ -74,7 +83,7 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
             }
         }
         // first valid entry of this lane and the row that holds it
-        const int64_t kf = k0 > S ? k0 : S;
+        const uint32_t kf = k0 > S ? k0 : S;
         const bool any = kf < E && kf < k0 + U;
         int r = 0;
         if (any) {
@@ -82,23 +91,24 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
             for (int step = 16; step > 0; step >>= 1)
                 if (r + step <= 31 && rs[r + step] <= kf) r += step;
         }
-        // walk the lane's entries, one FMA each, splitting at row ends
-        Ac part = Ac(0);
+        // walk the lane's entries, one FMA each, splitting at row ends; lane 0
+        // continues the running sum of a row begun in an earlier chunk
+        const bool head_from_left = any && kf > rs[r];
+        Ac part = (lane == 0 && head_from_left) ? racc[r] : Ac(0);
         int nseg = 0;                  // segments closed so far in this lane
         Ac head = Ac(0);
         int head_row = r;
-        bool head_from_left = any && kf > rs[r];
         int cur = r;
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-            const int64_t k = k0 + j;
+            const uint32_t k = k0 + j;
             if (k < kf || k >= E) continue;
             if (k >= rs[cur + 1]) {    // the current row ended before k
                 if (nseg == 0) {
                     head = part;
                     head_row = cur;
                 } else {
-                    racc[cur] += part; // a row that started and ended in this lane
+                    racc[cur] = part;  // a row that began and ended in this lane
                 }
                 ++nseg;
                 part = Ac(0);
@@ -106,13 +116,17 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
             }
             part = fma_acc(widen(val[j]), widen(ld_cached(x + col[j])), part);
         }
-        // segmented scan of the open tails across lanes
+        // segmented scan of the open tails across lanes; lanes without entries
+        // end any carry, so they count as segment heads, and so does lane 0
         const bool starts_here = any && (nseg > 0 || !head_from_left);
         Ac incl = part;
         bool flag = starts_here || !any;
-        // lanes without entries end any carry: treat them as segment heads
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
+        const unsigned heads = __ballot_sync(0xffffffffu, flag) | 1u;
+        const unsigned at_or_below = heads & (0xffffffffu >> (31 - lane));
+        const int dist = lane - (31 - __clz((int)at_or_below));   // lanes back to the head
+        const int span = __reduce_max_sync(0xffffffffu, dist);   // warp-uniform
+        // steps 1, 2, 4, ... up to span: the window 2^steps - 1 covers every run
+        for (int d = 1; d <= span; d <<= 1) {
             const Ac v_up = __shfl_up_sync(0xffffffffu, incl, d);
             const bool f_up = __shfl_up_sync(0xffffffffu, (int)flag, d) != 0;
             if (lane >= d) {
@@ -121,18 +135,17 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
             }
         }
         Ac carry = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) carry = Ac(0);
+        if (lane == 0 || !head_from_left) carry = Ac(0);
         if (any) {
-            const int64_t klast = (k0 + U < E ? k0 + U : E) - 1;
-            const bool tail_open = klast + 1 < rs[cur + 1];   // the row goes on
+            const uint32_t kend = k0 + U < E ? k0 + U : E;   // one past the lane's last entry
+            const bool tail_open = kend < rs[cur + 1];          // the row goes on
+            // the lane's first segment, joined to what the lanes before it hold
+            const Ac first = carry + (nseg > 0 ? head : part);
             if (nseg > 0) {
-                // the first segment ended inside this lane
-                racc[head_row] += (head_from_left ? carry : Ac(0)) + head;
-                if (!tail_open || lane == 31) racc[cur] += part;
-            } else {
-                // one segment only: row `cur`
-                const Ac total = (head_from_left ? carry : Ac(0)) + part;
-                if (!tail_open || lane == 31) racc[cur] += total;
+                racc[head_row] = first;                        // that row ends here
+                if (!tail_open || lane == 31) racc[cur] = part;
+            } else if (!tail_open || lane == 31) {
+                racc[cur] = first;
             }
         }
         __syncwarp();
