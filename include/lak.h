@@ -496,7 +496,10 @@ LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, in
  *      operands must not overlap across instances.
  * Ops: LAK_OP_AXPY (lak_axpy_desc), LAK_OP_DOT (lak_dot_desc; `out` is float
  * for F32/BF16/F16, double for F64), LAK_OP_GEMV_ROW (lak_gemv_desc, row-major
- * instances), LAK_OP_SPMV (lak_csr_desc, warp-segmented rows).  Per instance
+ * instances), LAK_OP_SPMV (lak_csr_desc, warp-segmented rows; its warps take
+ * 32-row blocks in order from a ticket counter in the workspace, so cfg.increment
+ * does not apply to it).  The dot and CSR batches keep counters in the
+ * workspace: one run of a batch at a time per workspace.  Per instance
  * the results equal those of the single-instance calls up to the order of
  * floating-point summation (axpy: identical).  The dot keeps at most
  * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).  A NULL cfg

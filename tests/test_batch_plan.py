@@ -61,6 +61,7 @@ def test_gemv_rows_per_unit_and_spmv_units(nat):
     c = [nat.CsrDesc(256, 512, 768, 1024, 1280, m, m, 5 * m) for m in (1, 64, 65, 1000)]
     info, offs, _ = plan(nat, "spmv", "f32", c, nat.LakCfg(64, 0, 4, 0))
     assert list(offs) == [0, 1, 2, 4, 20]
+    assert info.workspace_bytes == 65536          # the zero-filled ticket counters
 
 
 def test_gemv_plan_rejects_blocks_over_128(nat):

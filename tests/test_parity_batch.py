@@ -142,3 +142,48 @@ def test_batch_replays_from_cuda_graph():
         g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, first)
+
+
+def test_spmv_batch_ticket_counters_reset_between_runs():
+    """The CSR batch's warps take their rows from ticket counters in the
+    workspace, which the last warp resets: every run, direct or replayed from a
+    CUDA graph, must compute the product for the inputs it finds, and the
+    counter area must be zero again afterwards."""
+    csrs, xs, ys, hosts = [], [], [], []
+    for i, m in enumerate([1, 33, 4000, 20_000, 65]):
+        rp, ci, v = synth.banded_random_csr(m, 300 + i, 5, 64, "f32")
+        csrs.append((rp.cuda(), ci.cuda(), v.cuda(), m))
+        hosts.append((rp, ci, v))
+        xs.append(torch.empty(m, device="cuda"))
+        ys.append(torch.full((m,), float("nan"), device="cuda"))
+    b = B().spmv_batch(csrs, xs, ys)
+
+    def check(seed):
+        torch.cuda.synchronize()
+        for i, ((rp, ci, v), y) in enumerate(zip(hosts, ys)):
+            x = synth.uniform(rp.numel() - 1, seed + i, "f32")
+            assert_normwise(host(y), oracle.csr_spmv(rp, ci, v, x), "f32", f"instance {i}")
+        assert int(b.workspace[:16].count_nonzero()) == 0
+
+    def load(seed):
+        for i, x in enumerate(xs):
+            x.copy_(synth.uniform(x.numel(), seed + i, "f32").cuda())
+            ys[i].fill_(float("nan"))
+
+    for rep in range(3):
+        load(400 + 10 * rep)
+        b.run()
+        check(400 + 10 * rep)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    for rep in range(3):
+        load(500 + 10 * rep)
+        g.replay()
+        check(500 + 10 * rep)
