@@ -571,6 +571,30 @@ def run_batched(device, reps=10, count=4096, seed=4000):
     tot = sum(nb for _, _, nb in fams.values())
     report["all_families_one_graph"] = {"bytes": tot, "us": round(t_all * 1e3, 1),
                                         "GBs": round(tot / (t_all * 1e-3) / 1e9, 1)}
+    del g
+    # the CSR family's gather floor: one sparse inner product over all its
+    # entries, each instance's columns offset into the concatenation of the x
+    # vectors (the same gathers, in the same order, without the row structure)
+    offs, o = [], 0
+    for (_, _, _, m) in csrs:
+        offs.append(o)
+        o += m
+    vals = torch.cat([c[2] for c in csrs])
+    idx = torch.cat([c[1] + off for c, off in zip(csrs, offs)])
+    xall = torch.cat(cx)
+    res = torch.zeros(1, device=dev)
+    wsf = torch.zeros(lak.vec_dot_sparse_workspace(vals.numel(), "f32"), dtype=torch.uint8,
+                      device=dev)
+
+    def floor_call():
+        lak.vec_dot_sparse(vals, idx, xall, out=res, workspace=wsf)
+
+    floor_call()
+    t_f = _launch_ms(floor_call, reps)
+    report["spmv"]["entries"] = int(vals.numel())
+    report["spmv"]["gather_floor_us"] = round(t_f * 1e3, 1)
+    report["spmv"]["frac_gather_floor"] = round(t_f / (report["spmv"]["us_batched"] * 1e-3), 3)
+    del vals, idx, xall
     del ctypes
     return report
 
@@ -783,7 +807,7 @@ def run_formats(device, reps=20):
 
 def run_profile_set(device):
     """Every kernel family once, at sizes above L2 but a small device footprint
-    (~1.5 GB), for an ncu capture of all of them in one command.  Prints one
+    (under 5 GB), for an ncu capture of all of them in one command.  Prints one
     JSON line mapping each launch (in order) to its algorithmic bytes."""
     import torch
 
@@ -861,6 +885,19 @@ def run_profile_set(device):
     bg = B.gemv_batch(gA, gx, gy)
     rec("batch_gemv_f32", 4 * int(sum(int(a) * int(b) + int(a) + int(b) for a, b in zip(gm, gn))),
         bg.run)
+    del gA
+    # the first 256 instances of the batched leg's CSR family (same seeds)
+    cm = synth.log_uniform_ints(256, 1000, 200_000, 4005)
+    csrs, cxs, cys, cb = [], [], [], 0
+    for i, m in enumerate(cm):
+        m = int(m)
+        rp, ci, v = synth.device_csr_block_(m, 44000 + i, 5, 64, torch.float32, dev)
+        csrs.append((rp, ci, v, m))
+        cxs.append(synth.device_uniform_(torch.empty(m, device=dev), 64000 + i))
+        cys.append(torch.zeros(m, device=dev))
+        cb += v.numel() * 8 + (m + 1) * 4 + 2 * m * 4
+    bs = B.spmv_batch(csrs, cxs, cys)
+    rec("batch_spmv_f32", cb, bs.run)
     torch.cuda.synchronize()
     print(json.dumps({"profile_set": launches}))
     return 0

@@ -183,7 +183,7 @@ BatchCfg batch_row(lak_op op, lak_dtype dt) {
     switch (op) {
     case LAK_OP_AXPY: return {512, 64, LAK_INC_GLOBAL};
     case LAK_OP_DOT: return {512, f64 ? 32 : 16, LAK_INC_GLOBAL};
-    case LAK_OP_GEMV_ROW: return {128, 32, LAK_INC_GLOBAL};
+    case LAK_OP_GEMV_ROW: return {64, 32, LAK_INC_GLOBAL};   // 3.62 vs 3.76 ms at 128
     default: return {64, 16, LAK_INC_GLOBAL};      // CSR: 4 loads per lane (see batch_config)
     }
 }
