@@ -7,7 +7,8 @@ import torch
 
 import oracle
 import synth
-from checks import assert_dot, assert_normwise, assert_normwise_scaled, host
+from checks import (assert_dot, assert_normwise, assert_normwise_scaled, assert_reduced_sum,
+                    host)
 
 pytestmark = pytest.mark.gpu
 
@@ -94,6 +95,41 @@ def test_gemv_batch_vs_oracle(storage):
         abs_ref = oracle.gemv(np.nan_to_num(np.abs(oracle.widen(flat))), np.abs(host(x)), m, n,
                               lda, "row")
         assert_normwise_scaled(host(y), ref, abs_ref, storage, f"instance {i} {m}x{n}")
+
+
+@pytest.mark.parametrize("cfg", [None, (128, 0, 8, 0), (128, 0, 4, 0)])
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+def test_gemv_batch_long_rows_vs_oracle(storage, cfg):
+    """Rows long enough for the plan to give them whole warps (several warps per
+    row, added in warp order through shared memory), with padded leading
+    dimensions and odd lengths, next to short rows in the same batch."""
+    ms = sizes(18, 1, 300, 7, extra=(1, 3, 64))
+    ns = sizes(18, 1000, 6000, 8, extra=(2048, 2049, 4099, 8192))
+    dt = synth.torch_dtype(storage)
+    As, xs, ys, fulls = [], [], [], []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        m, n = int(m), int(n)
+        pad = 5 if i % 3 == 0 else 0
+        full = synth.normal((m, n + pad), 90 + i, storage).cuda()
+        fulls.append(full)
+        As.append(full[:, :n])
+        xs.append(synth.uniform(n, 190 + i, storage).cuda())
+        ys.append(torch.full((m,), float("nan"), dtype=dt, device="cuda"))
+    b = B().gemv_batch(As, xs, ys, cfg=cfg)
+    b.run()
+    torch.cuda.synchronize()
+    for i, (A, x, y) in enumerate(zip(As, xs, ys)):
+        m, n = A.shape
+        lda = fulls[i].shape[1]
+        flat = fulls[i].reshape(-1).cpu()
+        ref = oracle.gemv(flat, x.cpu(), m, n, lda, "row")
+        abs_ref = oracle.gemv(np.nan_to_num(np.abs(oracle.widen(flat))), np.abs(host(x)), m, n,
+                              lda, "row")
+        if storage == "bf16":                   # FP32 sums rounded once to BF16
+            assert_reduced_sum(host(y), ref, abs_ref, np.full(m, n), storage,
+                               f"instance {i} {m}x{n}")
+        else:
+            assert_normwise_scaled(host(y), ref, abs_ref, storage, f"instance {i} {m}x{n}")
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
