@@ -26,11 +26,11 @@ def test_resolve_follows_bucket():
     assert m.size_bucket("dot", "f64", 10 ** 8, 10 ** 8) == 3
     c1 = m.resolve_cfg("dot", "f64", 10 ** 6, 10 ** 6)
     c3 = m.resolve_cfg("dot", "f64", 10 ** 8, 10 ** 8)
-    assert (c1.block, c1.vec) == (512, 1) and c1.grid == min(sms(), -(-10 ** 6 // 512))
+    assert (c1.block, c1.vec) == (512, 4) and c1.grid == min(sms(), -(-10 ** 6 // (512 * 4)))
     assert (c3.block, c3.vec) == (256, 4) and c3.grid == 4 * sms()
     # column-major FP64 GEMV 2048^2 (33.6 MB, bucket 1): explicit grid from the table
     g = m.resolve_cfg("gemv_col", "f64", 2048, 2048)
-    assert g.block == 512 and g.vec == 2
+    assert g.block == 512 and g.vec == 4 and g.grid == 2 * sms()
     # BF16 takes the FP32 row's bytes per access: copy bucket 3 = 64 B -> 16 x 2 B... capped at 16
     b = m.resolve_cfg("copy", "bf16", 10 ** 9, 10 ** 9)
     assert b.vec == 16
