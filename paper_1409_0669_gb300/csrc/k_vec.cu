@@ -70,9 +70,10 @@ axpy_kernel(T *x, const T *y, const T *z, typename Acc<T>::type alpha, int64_t n
 // are added in FP64 and the block partial is stored in the workspace.  The
 // block whose arrival ticket is last adds all partials in FP64 in a fixed
 // order (strided per thread, then a shuffle tree), so the result does not
-// depend on which block happens to arrive last.  The ticket uses atomicInc
-// with wrap-around at gridDim.x - 1, so a completed call leaves the counter at
-// zero for the next call.
+// depend on which block happens to arrive last.  The ticket is an
+// acquire-release increment with wrap-around at gridDim.x - 1, so a completed
+// call leaves the counter at zero for the next call; a one-block grid writes
+// its sum directly.
 
 template <typename T, int V>
 __global__ void __launch_bounds__(512)

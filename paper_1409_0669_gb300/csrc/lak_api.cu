@@ -281,6 +281,9 @@ lak_status plan_vector(lak_op op, lak_dtype dt, int64_t n, const lak_cfg *cfg,
         const int per_sm = default_grid_per_sm(op, dt, bucket);
         const int64_t cap = per_sm > 0 ? (int64_t)per_sm * di->sms : waves_grid(di, c.block);
         grid = need < cap ? need : cap;
+        // an inner product one block covers in two passes skips the grid-wide
+        // combine (a ticket and a second block pass, ~2 us; a pass is less)
+        if (op == LAK_OP_DOT && need <= 2) grid = 1;
     }
     if (grid < 1) grid = 1;
     if (grid > 0x7fffffff) grid = 0x7fffffff;

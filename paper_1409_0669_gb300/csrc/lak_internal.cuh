@@ -337,11 +337,24 @@ template <typename A> __device__ __forceinline__ A group_sum(A v, int width) {
     return v;
 }
 
+// Arrival ticket at GPU scope, one instruction: the increment wraps back to 0
+// after `last`, release orders the caller's earlier stores (its block partial)
+// before it, and acquire orders the caller's later loads after every earlier
+// arrival's release.
+__device__ __forceinline__ unsigned int ticket_acq_rel(unsigned int *counter, unsigned int last) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.inc.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(counter), "r"(last) : "memory");
+    return old;
+}
+
 // Deterministic sum over the whole grid of one value per thread, written to
 // *out: a warp reduction in A, FP64 across the block's warps into one partial
 // per block, and the last block to arrive (ticket on *counter, which wraps
-// back to 0 for the next launch) adds the partials in block order.  Every
-// thread of every block must call it, as the kernel's last action.
+// back to 0 for the next launch) adds the partials in block order; a grid of
+// one block writes its sum directly (the same value: the last-block pass adds
+// only zeros to it).  Every thread of every block must call it, as the
+// kernel's last action.
 template <typename A, typename OutT>
 __device__ __forceinline__ void grid_sum_last_block(A v, OutT *out, unsigned int *counter,
                                                     double *partials) {
@@ -357,15 +370,19 @@ __device__ __forceinline__ void grid_sum_last_block(A v, OutT *out, unsigned int
         double b = lane < nwarps ? wsum[lane] : 0.0;
         b = group_sum(b, 32);
         if (lane == 0) {
-            partials[blockIdx.x] = b;
-            __threadfence();
-            const unsigned int ticket = atomicInc(counter, gridDim.x - 1);
-            am_last = (ticket == gridDim.x - 1);
+            if (gridDim.x == 1) {
+                *out = static_cast<OutT>(b);
+                am_last = 0;
+            } else {
+                partials[blockIdx.x] = b;
+                am_last = ticket_acq_rel(counter, gridDim.x - 1) == gridDim.x - 1;
+            }
         }
     }
     __syncthreads();
     if (!am_last) return;
-    __threadfence();
+    // thread 0's acquire saw every block's partial; the barrier above orders
+    // this block's reads of them after it
     double t = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + b);
     t = group_sum(t, 32);
