@@ -6,16 +6,25 @@
 // row is read with aligned wide streamed loads whatever the leading dimension.
 // x is read with wide cached loads when its matching offset is aligned too,
 // else element by element through L1 (it is re-read by every row).
+//
+// FP32 keeps V partial sums (independent FMA chains); FP64 keeps one chain in
+// acc[0]: on GB300 the FP64 pipe, not the FMA latency, bounds the FP64
+// product, and V partial sums would cost V - 1 extra FP64 adds per lane and
+// row (callers skip the combine when gemv_one_chain<T> holds).
 #pragma once
 
 #include "lak_internal.cuh"
 
 namespace lak {
 
+template <typename T>
+constexpr bool gemv_one_chain = sizeof(typename Acc<T>::type) == 8;
+
 template <typename T, int V>
 __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
                                               const T *__restrict__ Ar, const T *__restrict__ x,
                                               int64_t n, int lg, int G) {
+    using Ac = typename Acc<T>::type;
     constexpr int ES = (int)sizeof(T);
     constexpr int W = V * ES > 32 ? 32 : V * ES;
     const int64_t mis = (int64_t)(((uintptr_t)Ar % W) / ES);
@@ -34,7 +43,10 @@ __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
             load_pack<T, V, STREAM>(pa, Ab + c * V);
             load_pack<T, V, CACHED>(px, xb + c * V);
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[v]);
+            for (int v = 0; v < V; ++v) {
+                Ac &a = gemv_one_chain<T> ? acc[0] : acc[v];
+                a = fma_acc(widen(pa.e[v]), widen(px.e[v]), a);
+            }
         }
     } else {
 #pragma unroll 4
@@ -42,8 +54,10 @@ __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
             Pack<T, V> pa;
             load_pack<T, V, STREAM>(pa, Ab + c * V);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                acc[v] = fma_acc(widen(pa.e[v]), widen(ld_cached(xb + c * V + v)), acc[v]);
+            for (int v = 0; v < V; ++v) {
+                Ac &a = gemv_one_chain<T> ? acc[0] : acc[v];
+                a = fma_acc(widen(pa.e[v]), widen(ld_cached(xb + c * V + v)), a);
+            }
         }
     }
     for (int64_t j = nch * V + lg; j < nb; j += G)

@@ -247,10 +247,12 @@ gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = A(0);
             if (row < r1) row_group_dot<T, V>(acc, Am + row * lda, x, n, lg, G);
+            if constexpr (!gemv_one_chain<T>) {
 #pragma unroll
-            for (int w = 1; w < V; w <<= 1) {
+                for (int w = 1; w < V; w <<= 1) {
 #pragma unroll
-                for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+                    for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+                }
             }
             const A s = group_sum(acc[0], G);
             if (lg == 0 && row < r1) y[row] = narrow<T>(s);

@@ -78,10 +78,12 @@ gemv_row_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         Ac yold = Ac(0);
         if (beta != Ac(0) && lg == 0 && row < row_end) yold = widen(y[row]);
         if (row < row_end) row_group_dot<T, V>(acc, A + row * lda, x, n, lg, G);
+        if constexpr (!gemv_one_chain<T>) {
 #pragma unroll
-        for (int w = 1; w < V; w <<= 1) {
+            for (int w = 1; w < V; w <<= 1) {
 #pragma unroll
-            for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+                for (int v = 0; v + w < V; v += 2 * w) acc[v] += acc[v + w];
+            }
         }
         Ac s = acc[0];
         if (G <= 32) {
