@@ -47,7 +47,7 @@ from ._native import OPS as _OP_CODES
 from .timing import launch_time_us, warm_time_us
 
 OPS = ("copy", "axpy", "dot", "gemv_row", "gemv_col", "spmv")
-BLOCKS = (64, 128, 256, 512)
+BLOCKS = (32, 64, 128, 256, 512)
 VECS = (1, 2, 4, 8, 16)
 GRID_PER_SM = (0, 1, 2, 4, 8, 16, 32)       # 0 = automatic
 _L2_FLUSH_BYTES = 256 << 20
