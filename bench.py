@@ -1273,18 +1273,28 @@ def run_gb300(args):
         roofline["other"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
     roofline["traffic"] = recorded_traffic(args.traffic_json, dom_it)
 
-    # per (op, dtype) summary at the largest size, and the paper's points
+    # per (op, dtype) summary at the largest size, and the paper's points.
+    # Launches under 100 us are re-timed like the copy and the gather floor
+    # beside them (differential, L2 flushed): the sweep's per-launch events add
+    # the launch's start-up and the ~2 us event tick to them.
+    short = [name for name, (it, t) in per.items()
+             if t < 0.1 and it.size not in (2154435, 2048)]
+    with torch.cuda.stream(stream):
+        short_us = differential_us(per, short, device, lib_check)
     summary = {}
-    for name, (it, t) in per.items():
+    for name, (it, t_ev) in per.items():
         if it.size in (2154435, 2048):
             continue
         key = f"{it.op}_{name.split('_')[1]}_{it.dtype}" if it.op == "spmv" else \
             f"{it.op}_{it.dtype}"
+        t = short_us[name] * 1e-3 if name in short_us else t_ev
         gbs = it.nbytes / (t * 1e-3) / 1e9
         b, _ = roofline_of(it, t, peak, peak_kind, fp64_peak)
         summary[key] = {"size": it.size, "GBs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
                         "us": round(t * 1e3, 2), "bound": b["bound"],
                         "frac_bound": round(b["frac"], 4)}
+        if name in short_us:
+            summary[key]["us_events_in_sweep"] = round(t_ev * 1e3, 2)
     # the copy kernel moving the same number of bytes (cold): the streaming
     # ceiling at that size, launch and DRAM-latency ramp included
     with torch.cuda.stream(stream):
@@ -1319,7 +1329,7 @@ def run_gb300(args):
     # event tick, a fifth of a 10-us call
     pp_names = ("copy_f64_2154435", "axpy_f64_2154435", "dot_f64_2154435", "gemv_row_f64_2048")
     with torch.cuda.stream(stream):
-        pp_us = paper_points_us(per, pp_names, device, lib_check)
+        pp_us = differential_us(per, pp_names, device, lib_check)
     for name in pp_names:
         if name in per:
             it, t_ev = per[name]
@@ -1433,9 +1443,10 @@ def copy_at_bytes(sizes, device, lak, reps=10):
     return out
 
 
-def paper_points_us(per, names, device, lib_check, reps=20):
-    """Device time in us of each named sweep launch, L2 cold (differential
-    timing, like copy_at_bytes)."""
+def differential_us(per, names, device, lib_check, reps=20):
+    """Device time in us of each named sweep launch on its own, L2 cold
+    (differential timing, like copy_at_bytes): for launches short enough that
+    per-launch CUDA events would add their start-up and the event tick."""
     import torch
     from paper_1409_0669_gb300.timing import launch_time_us
     flush = torch.empty(64 << 20, dtype=torch.float32, device=device)
