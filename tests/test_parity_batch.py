@@ -132,8 +132,11 @@ def test_gemv_batch_long_rows_vs_oracle(storage, cfg):
             assert_normwise_scaled(host(y), ref, abs_ref, storage, f"instance {i} {m}x{n}")
 
 
+@pytest.mark.parametrize("cfg", [None, (32, 0, 4, 0), (128, 0, 8, 0), (512, 0, 4, 0)])
 @pytest.mark.parametrize("storage", ["f32", "f64"])
-def test_spmv_batch_vs_oracle(storage):
+def test_spmv_batch_vs_oracle(storage, cfg):
+    """Every launch shape maps tickets to (unit, warp slot) with its own warps
+    per block: one warp (32), four (128, 8 entries per lane) and sixteen (512)."""
     csrs, xs, ys, refs = [], [], [], []
     rows = sizes(24, 1000, 20_000, 5, extra=(1, 31, 33))
     for i, m in enumerate(rows):
@@ -149,7 +152,7 @@ def test_spmv_batch_vs_oracle(storage):
         xs.append(x.cuda())
         ys.append(torch.full((m,), float("nan"), dtype=v.dtype, device="cuda"))
         refs.append(oracle.csr_spmv(rp, ci, v, x))
-    b = B().spmv_batch(csrs, xs, ys)
+    b = B().spmv_batch(csrs, xs, ys, cfg=cfg)
     b.run()
     torch.cuda.synchronize()
     for i, (y, r) in enumerate(zip(ys, refs)):
