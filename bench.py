@@ -815,6 +815,7 @@ def run_profile_set(device):
     import synth
     from paper_1409_0669_gb300 import autograd as ag
     from paper_1409_0669_gb300 import batch as B
+    from paper_1409_0669_gb300.csr_bin import BinnedCsr
     from paper_1409_0669_gb300.sell import SellMatrix
 
     dev = device
@@ -835,6 +836,10 @@ def run_profile_set(device):
     rec("dot_f32", 8 * n, lambda: lak.vec_dot(y, z, workspace=ws))
     rec("dot_compensated_f32", 8 * n, lambda: lak.vec_dot_compensated(y, z, workspace=ws))
     rec("axpby_f32", 12 * n, lambda: lak.vec_axpby(x, 0.5, y, -1.5, z))
+    # the strided update on every second element (algorithmic bytes: the
+    # elements used; DRAM moves whole sectors, so about twice as many)
+    rec("axpby_strided2_f32", 12 * (n // 2),
+        lambda: lak.vec_axpby(x[::2], 0.5, y[::2], -1.5, z[::2]))
     rec("axpy_norm2_f32", 12 * n, lambda: lak.vec_axpy_norm2(x, y, z, 0.5, workspace=ws))
     rec("scale_dev_f32", 8 * n, lambda: lak.vec_scale_dev(y, out.fill_(2.0), out=x))
     rec("dot_noalloc_f32", 8 * n, lambda: lak.vec_dot_noalloc(y, z))
@@ -862,6 +867,8 @@ def run_profile_set(device):
         rec(f"spmv_csr_{nm}_f32", sb, lambda: lak.csr_spmv(rpd, cid, vd, xs, y=ys))
         S = SellMatrix(rpd, cid, vd, nc, sigma=sig)
         rec(f"spmv_sell_{nm}_f32", sb, lambda: S.spmv(xs, y=ys))
+        Bn = BinnedCsr(rpd, cid, vd, nc)
+        rec(f"spmv_binned_{nm}_f32", sb, lambda: Bn.spmv(xs, y=ys))
         dv = torch.empty(nnz, device=dev)
         rec(f"sampled_outer_{nm}_f32", nnz * 8 + (m + 1) * 4 + nc * 4 + m * 4,
             lambda: lak.csr_sampled_outer(rpd, cid, ys, xs, out=dv))
@@ -870,13 +877,16 @@ def run_profile_set(device):
         rec(f"gather_{nm}_f32", nnz * 12, lambda: lak.vec_gather(vd, perm, out=dv))
         rec(f"dot_sparse_{nm}_f32", nnz * 8,
             lambda: lak.vec_dot_sparse(vd, cid, xs, out=out, workspace=ws))
-        del S
+        del S, Bn
     ns = synth.log_uniform_ints(512, 65_536, 1_048_576, 1308)
     bx = [torch.empty(int(k), device=dev) for k in ns]
     byy = [synth.device_uniform_(torch.empty(int(k), device=dev), 1309) for k in ns]
     bz = [synth.device_uniform_(torch.empty(int(k), device=dev), 1310) for k in ns]
     bt = B.axpy_batch(bx, byy, bz, [0.5] * len(ns))
     rec("batch_axpy_f32", 12 * int(sum(int(k) for k in ns)), bt.run)
+    bouts = torch.zeros(len(ns), device=dev)
+    bd = B.dot_batch(byy, bz, [bouts[i:i + 1] for i in range(len(ns))])
+    rec("batch_dot_f32", 8 * int(sum(int(k) for k in ns)), bd.run)
     gm = synth.log_uniform_ints(256, 64, 4096, 1311)
     gn = synth.log_uniform_ints(256, 64, 4096, 1312)
     gA = [synth.device_normal_(torch.empty(int(a), int(b), device=dev), 1313) for a, b in zip(gm, gn)]
