@@ -143,10 +143,10 @@ constexpr DefaultCfg kDefaults[LAK_OP_COUNT][2][LAK_SIZE_BUCKETS] = {
     {{{256, 8, 8, G_}, {512, 4, 4, G_}, {512, 1, 16, G_}, {512, 2, 8, G_}},
      {{256, 1, 2, G_}, {512, 1, 4, G_}, {512, 2, 1, G_}, {256, 4, 4, G_}}},
     // row-major GEMV
-    {{{128, 16, 2, L_}, {512, 4, 8, L_}, {128, 8, 8, G_}, {64, 0, 8, G_}},
+    {{{256, 0, 2, G_}, {128, 8, 8, G_}, {32, 32, 8, G_}, {64, 0, 8, G_}},
      {{128, 8, 4, G_}, {32, 16, 8, G_}, {32, 0, 2, G_}, {32, 0, 8, G_}}},
     // column-major GEMV
-    {{{512, 0, 4, L_}, {512, 32, 16, G_}, {512, 2, 8, G_}, {128, 0, 4, G_}},
+    {{{512, 1, 4, L_}, {512, 0, 8, G_}, {512, 2, 8, L_}, {128, 0, 4, G_}},
      {{512, 4, 2, G_}, {512, 2, 4, G_}, {128, 8, 2, L_}, {512, 16, 2, L_}}},
     // CSR SpMV, group-per-row kernel (short and long rows)
     {{{256, 32, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}},
