@@ -149,7 +149,7 @@ constexpr DefaultCfg kDefaults[LAK_OP_COUNT][2][LAK_SIZE_BUCKETS] = {
     {{{512, 1, 4, L_}, {512, 0, 8, G_}, {512, 2, 8, L_}, {128, 0, 4, G_}},
      {{512, 4, 2, G_}, {512, 2, 4, G_}, {128, 8, 2, L_}, {512, 16, 2, L_}}},
     // CSR SpMV, group-per-row kernel (short and long rows)
-    {{{256, 32, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}},
+    {{{512, 2, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}},
      {{256, 0, 4, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}}},
 };
 
