@@ -93,3 +93,18 @@ def test_tune_buckets_small_space():
     for b in (0, 1):
         assert per[b]["cfg"] in [list(c.as_tuple()) for c in cands]
         assert per[b]["worst_ratio"] == 1.0
+
+
+def test_tiny_dot_runs_as_one_block():
+    """A dot whose automatic grid would be at most two blocks runs as one block
+    (no grid-wide combine); three blocks' worth keeps its grid.  FP64 bucket 0
+    reads 2 elements per access with 256 threads: 1024 elements are two blocks'
+    worth, 1537 three."""
+    m = lak()
+    assert m.resolve_cfg("dot", "f32", 1000, 1000).grid == 1
+    assert m.resolve_cfg("dot", "f64", 1024, 1024).grid == 1
+    assert m.resolve_cfg("dot", "f64", 1537, 1537).grid == 3
+    for dt, n in ((torch.float32, 1000), (torch.float64, 1024), (torch.float64, 1537)):
+        x = torch.ones(n, dtype=dt, device="cuda")
+        y = torch.full((n,), 0.5, dtype=dt, device="cuda")
+        assert float(m.vec_dot(x, y)) == n / 2          # exact: a sum of halves
