@@ -151,7 +151,7 @@ class Item:
     def __init__(self, name, op, dtype, size, nbytes, fn, args, h2d=(), d2h=()):
         self.name, self.op, self.dtype, self.size = name, op, dtype, size
         self.nbytes, self.fn, self.args = nbytes, fn, args
-        self.h2d, self.d2h = h2d, d2h      # (host, device) tensor pairs for the e2e leg
+        self.h2d, self.d2h = h2d, d2h      # device tensors the e2e leg fills / reads back
 
 
 def _aligned_slices(total_elems_list, dtype, device, align_elems):
@@ -1597,6 +1597,16 @@ def run_size_curves(device, reps=10):
     return out
 
 
+def e2e_copy_bytes(items):
+    """(host->device, device->host) bytes of one end-to-end step: every distinct
+    input tensor (same data pointer, length and dtype) once, every launch's
+    results each time."""
+    distinct = {(t.data_ptr(), t.numel(), t.dtype): t for it in items for t in it.h2d}
+    h2d = sum(t.numel() * t.element_size() for t in distinct.values())
+    d2h = sum(t.numel() * t.element_size() for it in items for t in it.d2h)
+    return h2d, d2h
+
+
 def run_e2e(items, keep, stream, device, steps, lib_check, dist):
     """The same step through the C ABI with inputs in pinned host memory: every
     step copies each distinct input host->device once (before its first
@@ -1624,9 +1634,7 @@ def run_e2e(items, keep, stream, device, steps, lib_check, dist):
 
     # every distinct input is copied once per step (copy, update and dot of one
     # size read the same y and z); every result is read back after its launch
-    h2d_bytes = sum(t.numel() * t.element_size()
-                    for t in {key_of(t): t for it in items for t in it.h2d}.values())
-    d2h_bytes = sum(t.numel() * t.element_size() for it in items for t in it.d2h)
+    h2d_bytes, d2h_bytes = e2e_copy_bytes(items)
     up = torch.cuda.Stream(device=device)
     down = torch.cuda.Stream(device=device)
 

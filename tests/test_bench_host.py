@@ -112,3 +112,27 @@ def test_reference_arm_runs_only_on_rank0(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"]) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_e2e_counts_each_distinct_input_once():
+    """The end-to-end step copies a shared input (the y and z read by copy,
+    update and dot of one size) once, and reads back every launch's result."""
+    sys.path.insert(0, ROOT)
+    import torch
+
+    import bench
+    y = torch.zeros(1000, dtype=torch.float32)
+    z = torch.zeros(1000, dtype=torch.float32)
+    x = torch.zeros(1000, dtype=torch.float32)
+    out = torch.zeros(1, dtype=torch.float32)
+    items = [bench.Item("copy", "copy", "f32", 1000, 8000, None, (), h2d=(y,), d2h=(x,)),
+             bench.Item("axpy", "axpy", "f32", 1000, 12000, None, (), h2d=(y, z), d2h=(x,)),
+             bench.Item("dot", "dot", "f32", 1000, 8000, None, (), h2d=(y, z), d2h=(out,))]
+    h2d, d2h = bench.e2e_copy_bytes(items)
+    assert h2d == 2 * 4000                   # y and z once each
+    assert d2h == 2 * 4000 + 4               # x after copy, x after axpy, the dot
+    # a view of the same storage with another length is another input
+    items.append(bench.Item("copy2", "copy", "f32", 500, 4000, None, (), h2d=(y[:500],),
+                            d2h=(x[:500],)))
+    h2d, _ = bench.e2e_copy_bytes(items)
+    assert h2d == 2 * 4000 + 2000
