@@ -1205,6 +1205,85 @@ def bind_to_gpu_numa(device):
     return {"pci": addr, "numa_node": node, "cpus": spec, "bound": True}
 
 
+HEADLINE_MAX_BYTES = 3072
+
+
+def _r(v, nd):
+    return None if v is None else round(float(v), nd)
+
+
+def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_step, launches,
+             roofline, per_kernel, e2e, cpu, clocks, detail_path):
+    """The one JSON line the run ends with: the headline metric and the keys a
+    reader needs to check it (roofline of the dominant kernel, per-kernel
+    GB/s at the largest sizes, end to end, CPU baseline, clocks), kept within
+    HEADLINE_MAX_BYTES.  Everything else goes to the detail file it names."""
+    rl = None
+    if roofline is not None:
+        rl = {k: roofline.get(k) for k in ("bound", "unit", "kernel")}
+        for k, nd in (("achieved", 4), ("peak", 4), ("frac", 4), ("share", 4),
+                      ("ms_per_launch", 5)):
+            rl[k] = _r(roofline.get(k), nd)
+        rl["traffic"] = roofline.get("traffic")
+        rl["bytes_per_launch"] = roofline.get("bytes_per_launch")
+        rl["flops_per_launch"] = roofline.get("flops_per_launch")
+        rl["peak_source"] = str(roofline.get("peak_source", ""))[:80]
+        other = roofline.get("other")
+        if other:
+            rl["other"] = {"bound": other.get("bound"), "unit": other.get("unit"),
+                           "achieved": _r(other.get("achieved"), 4),
+                           "peak": _r(other.get("peak"), 4), "frac": _r(other.get("frac"), 4)}
+    pk, pp = {}, {}
+    for key, v in (per_kernel or {}).items():
+        if key.startswith("paper_point_"):
+            pp[key[len("paper_point_"):]] = _r(v.get("GBs"), 1)
+            continue
+        ent = {"GBs": _r(v.get("GBs"), 1), "frac_hbm": _r(v.get("frac_hbm"), 3)}
+        if v.get("bound") not in (None, "hbm"):
+            ent["bound"] = v["bound"]
+            ent["frac_bound"] = _r(v.get("frac_bound"), 3)
+        pk[key] = ent
+    e2 = None
+    if e2e is not None:
+        e2 = {"value": _r(e2e.get("value"), 2), "unit": e2e.get("unit", "GB/s"),
+              "h2d_bytes_per_step": e2e.get("h2d_bytes_per_step"),
+              "d2h_bytes_per_step": e2e.get("d2h_bytes_per_step"),
+              "ms_per_step": _r(e2e.get("ms_per_step"), 3)}
+    cb = None
+    if cpu is not None:
+        cb = {"value": _r(cpu.get("value"), 3), "unit": cpu.get("unit", "GB/s"),
+              "cores": cpu.get("cores"), "kind": cpu.get("kind", "oracle"),
+              "sample": str(cpu.get("sample", ""))[:200]}
+        for k in ("all_cores", "plain_loop"):
+            if cpu.get(k):
+                cb[k] = {kk: (_r(vv, 3) if isinstance(vv, float) else vv)
+                         for kk, vv in cpu[k].items() if kk in ("value", "cores", "unit")}
+        if cpu.get("host"):
+            cb["host"] = str(cpu["host"])[:80]
+    ck = None
+    if clocks is not None:
+        ck = {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+              "reasons": clocks.get("reasons"), "samples": clocks.get("samples")}
+    line = {
+        "metric": METRIC, "value": _r(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": _r(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": workload, "bytes_per_step": bytes_per_step,
+                   "launches_per_step": launches,
+                   "l2": "no flush: inputs larger than L2, >1 GB of other traffic between "
+                         "two uses of a buffer",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": rl, "per_kernel": pk, "paper_points_GBs": pp, "e2e": e2,
+        "gpu_launches": launches * steps, "clocks": ck,
+    }
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    if detail_path:
+        line["detail"] = os.path.basename(detail_path)
+    return line
+
+
 def run_gb300(args):
     import torch
 
@@ -1393,38 +1472,26 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
 
-    line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
-        "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.only else f"subset /{args.only}/ of: "
-                   + WORKLOAD, "bytes_per_step": bytes_per_step,
-                   "launches_per_step": len(items),
-                   "l2": "cold at every launch without an explicit flush: launches are "
-                         "ordered so that more than 1 GB (8x L2) of other traffic passes "
-                         "between two uses of any buffer",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline, "per_kernel": summary, "e2e": e2e,
-        "gpu_launches": len(items) * K, "clocks": clocks,
-    }
-    if cpu is not None:
-        line["cpu_baseline"] = cpu
-    if precision is not None:
-        line["precision"] = precision
-    if batched is not None:
-        line["batched"] = batched
-    if autograd is not None:
-        line["autograd"] = autograd
-    if fused is not None:
-        line["fused"] = fused
-    if formats is not None:
-        line["spmv_formats"] = formats
-    if small is not None:
-        line["small_config"] = small
-    if curves is not None:
-        line["size_curves"] = curves
+    workload = WORKLOAD if not args.only else f"subset /{args.only}/ of: " + WORKLOAD
+    detail = {"per_kernel": summary, "roofline": roofline, "e2e": e2e, "clocks": clocks,
+              "config": {"workload": workload, "bytes_per_step": bytes_per_step,
+                         "launches_per_step": len(items)}}
+    for key, val in (("cpu_baseline", cpu), ("precision", precision), ("batched", batched),
+                     ("autograd", autograd), ("fused", fused), ("spmv_formats", formats),
+                     ("small_config", small), ("size_curves", curves)):
+        if val is not None:
+            detail[key] = val
+    detail_path = None
+    if rank == 0 and args.detail_json:
+        detail_path = args.detail_json
+        with open(detail_path, "w") as fh:
+            json.dump(detail, fh, indent=1)
+    line = headline(value=value, ms_per_step=ms_per_step, steps=K, warmup=W, world=world,
+                    workload=workload, bytes_per_step=bytes_per_step,
+                    launches=len(items), roofline=roofline, per_kernel=summary, e2e=e2e,
+                    cpu=cpu, clocks=clocks, detail_path=detail_path)
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, separators=(",", ":")))
     if dist is not None:
         dist.destroy_process_group()
     del keep
@@ -1742,6 +1809,10 @@ def main(argv=None):
                     help="regex: run (and allocate) only the launches whose name matches "
                          "(profiling captures); the result is then not the full workload")
     ap.add_argument("--sweep-json", default=None, help="write the per-size table here")
+    ap.add_argument("--detail-json", default=os.path.join(os.getcwd(), "bench_detail.json"),
+                    help="write the full report (every per-kernel entry, the precision, "
+                         "batched, autograd, fused, format, small-configuration and size-curve "
+                         "sections) here; the printed line names this file ('' = none)")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "dram_traffic.json"),
                     help="per-kernel DRAM bytes per launch recorded from an ncu capture")
     args = ap.parse_args(argv)

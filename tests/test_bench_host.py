@@ -136,3 +136,80 @@ def test_e2e_counts_each_distinct_input_once():
                             d2h=(x[:500],)))
     h2d, _ = bench.e2e_copy_bytes(items)
     assert h2d == 2 * 4000 + 2000
+
+
+def _fake_run_parts(bench):
+    """The pieces of a full-size run's report, filled with long-decimal values
+    (the worst case for the printed length)."""
+    import math
+    v = math.pi * 1000.0
+    per = {}
+    for op in ("copy", "axpy", "dot", "gemv_row", "gemv_col"):
+        for dt in ("f32", "f64"):
+            per[f"{op}_{dt}"] = {"size": 100000000, "GBs": v, "frac_hbm": v / 7000.0,
+                                 "us": v / 9.0, "bound": "alu" if dt == "f64" else "hbm",
+                                 "frac_bound": 0.123456789, "copy_same_bytes_GBs": v,
+                                 "frac_copy_same_bytes": 0.987654321}
+    for mat in ("lap3d", "powerlaw"):
+        for dt in ("f32", "f64"):
+            per[f"spmv_{mat}_{dt}"] = {"size": 2097152, "GBs": v, "frac_hbm": 0.7777777,
+                                       "us": 43.123456, "bound": "gather", "frac_bound": 0.81,
+                                       "gather_floor_us": 33.3333, "frac_gather_floor": 0.8,
+                                       "us_events_in_sweep": 45.555}
+    for name in ("copy_f64_2154435", "axpy_f64_2154435", "dot_f64_2154435",
+                 "gemv_row_f64_2048"):
+        per["paper_point_" + name] = {"GBs": v, "us": 9.87654, "us_events_in_sweep": 12.3456,
+                                      "copy_same_bytes_GBs": v, "frac_copy_same_bytes": 0.99}
+    roof = {"bound": "alu", "achieved": 1.1601234567, "peak": 1.2586012345,
+            "unit": "TFLOP/s", "frac": 0.9217654321, "traffic": 2148597760,
+            "kernel": "gemv_row_f64_16384", "share": 0.0961234567,
+            "bytes_per_launch": 2147745792, "flops_per_launch": 536870912.0,
+            "ms_per_launch": 0.46271234567,
+            "peak_source": "measured: FP64 FMA probe (independent chains) x SMs at the "
+                           "median SM clock under load, and more words to be cut",
+            "other": {"bound": "hbm", "achieved": 4641.123456, "peak": 6785.9, "unit": "GB/s",
+                      "frac": 0.683987654}}
+    e2e = {"value": 349.987654321, "unit": "GB/s", "h2d_bytes_per_step": 14123456789,
+           "d2h_bytes_per_step": 4512345678, "ms_per_step": 72.4123456,
+           "steps": 5, "rounds_ms_per_step": [72.1, 72.4, 73.0], "pipeline": "x" * 300,
+           "host_binding": "cpus 0-71"}
+    cpu = {"value": 6.612345678, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": "s" * 600,
+           "all_cores": {"value": 98.7654321, "cores": 72, "unit": "GB/s", "sample": "t" * 300},
+           "plain_loop": {"value": 25.4321, "cores": 1, "unit": "GB/s", "sample": "u" * 300},
+           "host": "Neoverse-V2 " + "h" * 200}
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 512}
+    return per, roof, e2e, cpu, clocks
+
+
+def test_headline_is_compact_and_complete():
+    """The run's last stdout line stays small enough for a log tail to hold it
+    whole, and carries the headline, roofline, end-to-end, CPU-baseline and
+    clock keys; the large sections stay out of it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    per, roof, e2e, cpu, clocks = _fake_run_parts(bench)
+    line = bench.headline(value=5266.123456789, ms_per_step=4.8123456789, steps=20, warmup=5,
+                          world=1, workload=bench.WORKLOAD, bytes_per_step=25312345678,
+                          launches=124, roofline=roof, per_kernel=per, e2e=e2e, cpu=cpu,
+                          clocks=clocks, detail_path="/some/where/bench_detail.json")
+    text = json.dumps(line, separators=(",", ":"))
+    assert len(text.encode()) <= bench.HEADLINE_MAX_BYTES, len(text)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "per_kernel", "e2e", "cpu_baseline", "clocks", "gpu_launches"):
+        assert key in line, key
+    assert line["config"]["workload"] == bench.WORKLOAD
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in line["roofline"], key
+    for key in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert key in line["e2e"], key
+    for key in ("value", "unit", "cores", "kind", "sample"):
+        assert key in line["cpu_baseline"], key
+    assert set(line["per_kernel"]) == {k for k in per if not k.startswith("paper_point_")}
+    assert line["gpu_launches"] == 124 * 20
+    assert line["detail"] == "bench_detail.json"
+    for big in ("precision", "batched", "autograd", "fused", "spmv_formats", "small_config",
+                "size_curves"):
+        assert big not in line
+    assert json.loads(text)["value"] == round(5266.123456789, 2)
