@@ -136,14 +136,18 @@ dot_comp_kernel(double *out, const T *__restrict__ x, const T *__restrict__ y, i
 #pragma unroll
     for (int v = 0; v < V; ++v) sv[v] = cv[v] = 0.0f;
 
+    // Every operation is an explicitly rounded intrinsic: nvcc contracts a plain
+    // `s + a * b` into one FMA under its default --fmad=true, which would make
+    // t = fma(a, b, s) and f no longer the exact error of s + p.  The _rn
+    // intrinsics are never contracted.
     auto add = [](float &s, float &c, float a, float b) {
-        const float p = a * b;
+        const float p = __fmul_rn(a, b);
         const float e = __fmaf_rn(a, b, -p);      // a*b = p + e exactly
-        const float t = s + p;                    // TwoSum(s, p) = t + f
-        const float bv = t - s;
-        const float f = (s - (t - bv)) + (p - bv);
+        const float t = __fadd_rn(s, p);          // TwoSum(s, p) = t + f
+        const float bv = __fsub_rn(t, s);
+        const float f = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
         s = t;
-        c += f + e;
+        c = __fadd_rn(c, __fadd_rn(f, e));
     };
 
     const Range r = chunk_range(nchunks, inc);
