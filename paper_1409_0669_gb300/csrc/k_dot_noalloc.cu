@@ -74,24 +74,17 @@ extern "C" LAK_API lak_status vec_dot_noalloc(void *out, const void *x, const vo
     if ((uintptr_t)x % es || (uintptr_t)y % es)
         return fail(LAK_EINVAL, "vec_dot_noalloc: pointers not aligned to the element size");
 
-    // the launch vec_dot would make: configuration, then the vector width the
-    // pointers' alignment allows, then the grid for that width
-    lak_cfg r{};
-    lak_status st = lak_resolve_cfg(LAK_OP_DOT, dtype, n, n, 0, cfg, &r);
-    if (st != LAK_OK) return st;
-    const void *ptrs[2] = {x, y};
+    // exactly the launch vec_dot makes for these operands, so both sum in the
+    // same block order and give the same bits
+    lak::Launch L{};
     int64_t head = 0;
-    const int vec = lak::pick_vec(r.vec, es, ptrs, 2, n, &head);
-    if (vec != r.vec) {
-        const lak_cfg c2{r.block, (cfg && cfg->block != 0) ? cfg->grid : 0, vec, r.increment};
-        st = lak_resolve_cfg(LAK_OP_DOT, dtype, n, n, 0, &c2, &r);
-        if (st != LAK_OK) return st;
-    }
-    if (r.grid > LAK_DOT_NOALLOC_MAX_BLOCKS)
+    lak_status st = lak::plan_dot("vec_dot_noalloc", dtype, n, cfg, x, y, &L, &head);
+    if (st != LAK_OK) return st;
+    if (L.grid > LAK_DOT_NOALLOC_MAX_BLOCKS)
         return fail(LAK_EINVAL,
                     "vec_dot_noalloc: %d blocks exceed the built-in scratch, which holds %d "
                     "block partials; pass a cfg with grid <= %d or use vec_dot with a workspace",
-                    r.grid, LAK_DOT_NOALLOC_MAX_BLOCKS, LAK_DOT_NOALLOC_MAX_BLOCKS);
+                    L.grid, LAK_DOT_NOALLOC_MAX_BLOCKS, LAK_DOT_NOALLOC_MAX_BLOCKS);
 
     void *scratch = nullptr;
     st = scratch_on_current_device(&scratch);
@@ -101,6 +94,5 @@ extern "C" LAK_API lak_status vec_dot_noalloc(void *out, const void *x, const vo
     const cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess)
         return fail(LAK_ECUDA, "vec_dot_noalloc: clearing the counter: %s", cudaGetErrorString(e));
-    const lak::Launch L{r.block, r.grid, vec, r.increment};
     return lak::launch_dot(dtype, out, x, y, n, scratch, L, head, s);
 }

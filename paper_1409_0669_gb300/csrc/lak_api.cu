@@ -451,6 +451,19 @@ lak_cfg batch_config(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
     return c;
 }
 
+lak_status plan_dot(const char *who, lak_dtype dt, int64_t n, const lak_cfg *cfg, const void *x,
+                    const void *y, Launch *L, int64_t *head) {
+    lak_status st = check_cfg(cfg, who);
+    if (st != LAK_OK) return st;
+    const void *ptrs[2] = {x, y};
+    VecPlan p;
+    st = plan_vector(LAK_OP_DOT, dt, n, cfg, ptrs, 2, &p);
+    if (st != LAK_OK) return st;
+    *L = p.L;
+    *head = p.head;
+    return LAK_OK;
+}
+
 int pick_vec(int want, int es, const void *const *ptrs, int nptrs, int64_t n, int64_t *head) {
     for (int vec = want; vec > 1; vec >>= 1) {
         const int w = access_bytes(vec, es);

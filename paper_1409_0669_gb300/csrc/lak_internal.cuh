@@ -106,6 +106,13 @@ lak_cfg batch_config(lak_op op, lak_dtype dt, const lak_cfg *cfg);
 // prologue length (elements) in *head.
 int pick_vec(int want, int es, const void *const *ptrs, int nptrs, int64_t n, int64_t *head);
 
+// The launch vec_dot makes for these operands (configuration, the vector
+// width both pointers' alignment allows, the grid for that width) and its
+// scalar prologue length; other entry points that run the dot kernel take it
+// from here so that they sum in the same block order.
+lak_status plan_dot(const char *who, lak_dtype dt, int64_t n, const lak_cfg *cfg, const void *x,
+                    const void *y, Launch *L, int64_t *head);
+
 // Launchers (one per kernel family), called after validation.
 lak_status launch_copy(void *x, const void *y, int64_t n, int es, const Launch &L,
                        int64_t head, cudaStream_t s);

@@ -14,7 +14,7 @@ import torch
 
 import oracle
 import synth
-from checks import TOL, assert_dot, host
+from checks import assert_dot, host
 
 pytestmark = pytest.mark.gpu
 
@@ -25,30 +25,37 @@ def _lib():
     return _native
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
-def test_noalloc_matches_vec_dot_on_consecutive_calls(storage):
+@pytest.mark.parametrize("offset", [0, 1], ids=["aligned", "offset1"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+def test_noalloc_matches_vec_dot_on_consecutive_calls(storage, offset):
+    """Same bits as vec_dot (both plan the same launch, so the blocks sum in
+    the same order), two calls in a row at each length, lengths changing from
+    call to call so that each call meets the scratch the previous one left.
+    offset = 1 starts both operands one element past an aligned address, where
+    the launch narrows its vector width and adds a scalar prologue."""
     nat = _lib()
     lib = nat.load()
     import paper_1409_0669_gb300 as lak
     code = nat.DTYPES[storage]
     stream = torch.cuda.current_stream().cuda_stream
     odt = torch.float64 if storage == "f64" else torch.float32
-    # different lengths back to back: the second call reuses the scratch the
-    # first one left behind
-    for n, seed in ((3_000_017, 1), (1001, 2), (3_000_017, 3)):
-        x = synth.uniform(n, seed, storage).cuda()
-        y = synth.uniform(n, seed + 50, storage).cuda()
+    for n, seed in ((3_000_017, 1), (1001, 2), (0, 3), (1, 4), (33, 5), (3_000_017, 6)):
+        xb = synth.uniform(n + offset, seed, storage).cuda()
+        yb = synth.uniform(n + offset, seed + 50, storage).cuda()
+        x, y = xb[offset:], yb[offset:]
         ref = lak.vec_dot(x, y).item()                       # workspace-based entry point
         for _ in range(2):                                   # two calls in a row
             out = torch.full((1,), float("nan"), dtype=odt, device="cuda")
-            st = lib.vec_dot_noalloc(out.data_ptr(), x.data_ptr(), y.data_ptr(), n, code, None,
-                                     stream)
+            st = lib.vec_dot_noalloc(out.data_ptr(), x.data_ptr() if n else None,
+                                     y.data_ptr() if n else None, n, code, None, stream)
             nat.check("vec_dot_noalloc", st)
             torch.cuda.synchronize()
             got = out.item()
+            assert got == ref, (n, got, ref)                 # bit-identical to vec_dot
+            if n == 0:
+                assert got == 0.0
+                continue
             xs, ys = host(x), host(y)
-            scale = float((xs * xs).sum() ** 0.5 * (ys * ys).sum() ** 0.5)
-            assert abs(got - ref) <= TOL[storage] * scale
             assert_dot(got, oracle.dot(x.cpu(), y.cpu()), xs, ys, storage)
 
 
