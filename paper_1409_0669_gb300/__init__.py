@@ -75,20 +75,41 @@ def storage_of(t: torch.Tensor) -> str:
 _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
 
 
+_current_device = getattr(torch._C, "_cuda_getDevice", None) or torch.cuda.current_device
+
+
 def _stream(stream) -> int:
     if stream is None:
         if _raw_stream is not None:
-            return _raw_stream(torch.cuda.current_device())
+            return _raw_stream(_current_device())
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, torch.cuda.Stream):
+        if stream.device.index != _current_device():
+            raise ValueError(f"stream is on {stream.device} but the current device is "
+                             f"cuda:{_current_device()}")
         return stream.cuda_stream
     return int(stream)
 
 
 def _dev_ptr(t: torch.Tensor, name: str) -> int:
+    """Device address of an operand.  The library launches on the current
+    device (and finds per-device state such as built-in scratch through it),
+    so an operand on another device is refused here rather than handed to a
+    kernel running elsewhere."""
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    cur = _current_device()
+    if t.device.index != cur:
+        raise ValueError(f"{name} is on {t.device} but the current device is cuda:{cur}; "
+                         f"call under `with torch.cuda.device({t.device.index}):`")
     return t.data_ptr()
+
+
+def _on_current_device(*ts):
+    """Refuse CUDA tensors on a device other than the current one (see _dev_ptr)."""
+    for t in ts:
+        if t is not None and t.numel() > 0:
+            _dev_ptr(t, "operand")
 
 
 def _vec_arg(t: torch.Tensor, name: str):
@@ -543,6 +564,6 @@ def vec_scale_dev(v: torch.Tensor, alpha: torch.Tensor, out: Optional[torch.Tens
         out = torch.empty_like(v)
     n = v.numel()
     st = _lib.vec_scale_dev(_vec_arg(out, "out") if n else None, _vec_arg(v, "v") if n else None,
-                            alpha.data_ptr(), n, DTYPES[s], _stream(stream))
+                            _dev_ptr(alpha, "alpha"), n, DTYPES[s], _stream(stream))
     _native.check("vec_scale_dev", st)
     return out

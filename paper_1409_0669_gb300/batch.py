@@ -23,7 +23,8 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
         return None
     if not t.is_cuda:
         raise ValueError("batched operands must be CUDA tensors")
-    return t.data_ptr()
+    from . import _dev_ptr
+    return _dev_ptr(t, "batched operand")
 
 
 def _cfg(cfg):
@@ -60,6 +61,8 @@ class Batch:
         return int(self.info.total_units)
 
     def run(self, stream=None):
+        from . import _on_current_device
+        _on_current_device(self.table, self.workspace)
         sh = (torch.cuda.current_stream().cuda_stream if stream is None else
               (stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)))
         st = self._lib.lak_batch_run(ctypes.byref(self.info), self.table.data_ptr(),

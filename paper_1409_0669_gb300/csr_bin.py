@@ -9,7 +9,7 @@ from typing import Optional
 
 import torch
 
-from . import _cfg_ptr, _native, _stream, storage_of
+from . import _cfg_ptr, _native, _on_current_device, _stream, storage_of
 from ._native import DTYPES
 
 BINS = 7            # LAK_CSR_BINS
@@ -21,6 +21,7 @@ class BinnedCsr:
                  n_cols: int, stream=None):
         if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
             raise TypeError("row_ptr and col_idx must be int32")
+        _on_current_device(row_ptr, col_idx, vals)
         lib = _native.load()
         self._lib = lib
         dev = row_ptr.device
@@ -44,6 +45,7 @@ class BinnedCsr:
             raise TypeError("x must have the matrix's dtype")
         if y is None:
             y = torch.empty(self.m, dtype=self.vals.dtype, device=self.vals.device)
+        _on_current_device(x, y, self.row_ptr)
         _native.check("csr_bin_spmv",
                       self._lib.csr_bin_spmv(y.data_ptr() if self.m else None,
                                              self.row_ptr.data_ptr(),

@@ -10,13 +10,14 @@ from typing import Optional
 
 import torch
 
-from . import _cfg_ptr, _native, _stream, storage_of
+from . import _cfg_ptr, _native, _on_current_device, _stream, storage_of
 from ._native import DTYPES
 
 
 class SellMatrix:
     def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor,
                  n_cols: int, sigma: int = 1, stream=None):
+        _on_current_device(row_ptr, col_idx, vals)
         lib = _native.load()
         self._lib = lib
         dev = row_ptr.device
@@ -49,6 +50,7 @@ class SellMatrix:
     def pack(self, vals: torch.Tensor, stream=None):
         """(Re)load the CSR values into the SELL slots."""
         s = storage_of(vals)
+        _on_current_device(vals, self.vals)
         _native.check("sell_pack_values",
                       self._lib.sell_pack_values(self.vals.data_ptr(),
                                                  vals.data_ptr() if vals.numel() else None,
@@ -62,6 +64,7 @@ class SellMatrix:
             raise TypeError("x must have the matrix's dtype")
         if y is None:
             y = torch.empty(self.m, dtype=self.vals.dtype, device=self.vals.device)
+        _on_current_device(x, y, self.vals)
         _native.check("sell_spmv",
                       self._lib.sell_spmv(y.data_ptr() if self.m else None,
                                           self.slice_ptr.data_ptr(), self.slice_len.data_ptr(),

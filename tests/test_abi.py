@@ -152,3 +152,44 @@ def test_python_binding_imports_and_fails_loudly_without_library(tmp_path):
     from paper_1409_0669_gb300 import _native
     with pytest.raises(ImportError, match="no CPU fallback"):
         _native.load(str(tmp_path / "missing.so"))
+
+
+class _FakeCudaTensor:
+    """Just enough of a CUDA tensor for the binding's operand checks."""
+    is_cuda = True
+
+    def __init__(self, index, n=4):
+        import torch
+        self.device = torch.device("cuda", index)
+        self._n = n
+
+    def numel(self):
+        return self._n
+
+    def dim(self):
+        return 1
+
+    def stride(self, d):
+        return 1
+
+    def data_ptr(self):
+        return 0x7000_0000_0000
+
+
+def test_binding_refuses_operands_on_another_device(lib, monkeypatch):
+    """The library launches on the current device; the binding refuses an
+    operand on any other device instead of passing its address to a kernel
+    that runs elsewhere (no GPU needed: the check runs before any call)."""
+    import paper_1409_0669_gb300 as m
+    monkeypatch.setattr(m, "_current_device", lambda: 0)
+    assert m._dev_ptr(_FakeCudaTensor(0), "x") == 0x7000_0000_0000
+    with pytest.raises(ValueError, match="cuda:1 but the current device is cuda:0"):
+        m._dev_ptr(_FakeCudaTensor(1), "x")
+    with pytest.raises(ValueError, match="cuda:1"):
+        m._vec_arg(_FakeCudaTensor(1), "y")
+    with pytest.raises(ValueError):
+        m._on_current_device(_FakeCudaTensor(0), _FakeCudaTensor(1))
+    m._on_current_device(_FakeCudaTensor(0), _FakeCudaTensor(1, n=0), None)   # empty: no address
+    from paper_1409_0669_gb300 import batch
+    with pytest.raises(ValueError, match="cuda:1"):
+        batch._ptr(_FakeCudaTensor(1))
