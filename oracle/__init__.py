@@ -81,6 +81,7 @@ def _bind(path: str):
         "orc_dense_outer": (None, [_F64P, _F64P, _F64P, _I64, _I64, _I64]),
         "orc_sampled_outer": (None, [_F64P, _I32P, _I32P, _F64P, _F64P, _I64]),
         "orc_round_bf16": (None, [_U16P, _F32P, _I64]),
+        "orc_round_bf16_f64": (None, [_U16P, _F64P, _I64]),
         "orc_widen_bf16": (None, [_F64P, _U16P, _I64]),
         "orc_round_f16": (None, [_U16P, _F64P, _I64]),
         "orc_widen_f16": (None, [_F64P, _U16P, _I64]),
@@ -338,6 +339,14 @@ def round_bf16(v_f32) -> np.ndarray:
     return out
 
 
+def round_bf16_f64(v) -> np.ndarray:
+    """double values -> BF16 bit patterns (uint16), one round to nearest even."""
+    vv = widen(v)
+    out = np.empty(vv.size, np.uint16)
+    _load().orc_round_bf16_f64(_ptr(out, _U16P), _ptr(vv, _F64P), vv.size)
+    return out
+
+
 def round_f16(v) -> np.ndarray:
     """double values -> IEEE binary16 bit patterns (uint16), round to nearest even."""
     vv = widen(v)
@@ -367,7 +376,7 @@ def round_to(v, storage: str) -> np.ndarray:
     if storage == "f32":
         return round_f32(v).astype(np.float64)
     if storage == "bf16":
-        return widen_bf16_bits(round_bf16(round_f32(v)))
+        return widen_bf16_bits(round_bf16_f64(v))
     if storage == "f16":
         return widen_f16_bits(round_f16(v))
     raise ValueError(storage)

@@ -396,6 +396,43 @@ void orc_round_bf16(uint16_t *out, const float *in, int64_t n)
     }
 }
 
+/*
+ * double -> BF16 bit patterns with round-to-nearest-even, in one rounding of
+ * the double itself (not through FP32, whose own rounding can move a value
+ * onto a BF16 midpoint).  BF16 is FP32's layout with 7 fraction bits: normal
+ * values 1.f * 2^e for e in [-126, 127], subnormal spacing 2^-133; values at
+ * or above (2 - 2^-8) * 2^127 round to infinity.
+ */
+void orc_round_bf16_f64(uint16_t *out, const double *in, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double v = in[i];
+        uint16_t sign = signbit(v) ? 0x8000u : 0u;
+        double a = fabs(v);
+        if (isnan(v)) { out[i] = (uint16_t)(sign | 0x7fc0u); continue; }
+        if (a >= ldexp(2.0 - ldexp(1.0, -8), 127)) { out[i] = (uint16_t)(sign | 0x7f80u); continue; }
+        int e;
+        frexp(a, &e);                     /* a = f * 2^e, f in [0.5, 1) */
+        int exp_unb = e - 1;              /* a = 1.x * 2^exp_unb */
+        double quantum = (exp_unb < -126) ? ldexp(1.0, -133) : ldexp(1.0, exp_unb - 7);
+        double r = nearbyint(a / quantum);   /* exact scaling; nearest-even */
+        double h = r * quantum;
+        uint16_t bits;
+        if (h == 0.0) {
+            bits = 0;
+        } else if (h < ldexp(1.0, -126)) {
+            bits = (uint16_t)r;           /* subnormal: fraction = r */
+        } else {
+            int he;
+            double hf = frexp(h, &he);    /* h = hf * 2^he */
+            int biased = he - 1 + 127;
+            uint32_t frac = (uint32_t)((hf * 2.0 - 1.0) * 128.0);
+            bits = (uint16_t)((biased << 7) | frac);
+        }
+        out[i] = (uint16_t)(sign | bits);
+    }
+}
+
 /* BF16 -> double, exact. */
 void orc_widen_bf16(double *out, const uint16_t *in, int64_t n)
 {

@@ -548,6 +548,63 @@ def pin_round_bf16():
         torch.bfloat16).to(torch.float64).numpy())
 
 
+def _bf16_nearest_bits(v: float) -> int:
+    """Correctly rounded BF16 (nearest, ties to even) of a finite double, by
+    exact rational arithmetic on the BF16 grid: 8 significant bits, exponents
+    down to -126, subnormal spacing 2^-133, overflow to infinity at and above
+    (2 - 2^-8) * 2^127."""
+    from fractions import Fraction
+    sign = 0x8000 if math.copysign(1.0, v) < 0 else 0
+    a = Fraction(abs(v))
+    if a >= Fraction(2 ** 9 - 1, 2 ** 8) * 2 ** 127:
+        return sign | 0x7F80
+    if a == 0:
+        return sign
+    e = math.floor(math.log2(abs(v)))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    q = Fraction(2) ** (max(e, -126) - 7)
+    k = a / q
+    lo = math.floor(k)
+    rem = k - lo
+    r = lo + 1 if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and lo % 2 == 1) else lo
+    h = r * q
+    if h < Fraction(2) ** -126:
+        return sign | r
+    he = max(e, -126)
+    if h >= Fraction(2) ** (he + 1):                   # carried into the next binade
+        he += 1
+        r //= 2
+    return sign | ((he + 127) << 7) | (r - 128)
+
+
+def pin_round_bf16_f64():
+    """Direct FP64 -> BF16 rounding: equals torch's conversion on FP32 values
+    (one rounding either way), equals an exact rational rounding on random
+    doubles, and differs from rounding through FP32 where that route lands on a
+    BF16 midpoint (1 + 2^-8 + 2^-40 must go up to 1 + 2^-7)."""
+    f32 = _bf16_cases()
+    f32 = f32[~np.isnan(f32)]
+    assert np.array_equal(oracle.round_bf16_f64(f32.astype(np.float64)), oracle.round_bf16(f32))
+    g = synth.rng(41)
+    rnd = g.standard_normal(3000) * 2.0 ** g.integers(-140, 128, 3000)
+    mid = (2 * g.integers(128, 256, 1000) + 1) * 2.0 ** g.integers(-130, 120, 1000)
+    nudged = np.concatenate([mid * (1 + 2.0 ** -40), mid * (1 - 2.0 ** -40), mid])
+    big = np.array([(2 - 2.0 ** -8) * 2.0 ** 127, np.nextafter((2 - 2.0 ** -8) * 2.0 ** 127, 0),
+                    2.0 ** -133, 2.0 ** -134, 3 * 2.0 ** -135, 2.0 ** -126, -0.0, 1e-300])
+    v = np.concatenate([rnd, nudged, -nudged, big])
+    v = v[np.isfinite(v)]
+    got = oracle.round_bf16_f64(v)
+    ref = np.array([_bf16_nearest_bits(float(t)) for t in v], np.uint16)
+    assert np.array_equal(got, ref)
+    trap = 1.0 + 2.0 ** -8 + 2.0 ** -40
+    assert oracle.widen_bf16_bits(oracle.round_bf16_f64([trap]))[0] == 1.0 + 2.0 ** -7
+    assert oracle.widen_bf16_bits(oracle.round_bf16(np.float32(trap)))[0] == 1.0
+    assert np.array_equal(oracle.round_to([trap], "bf16"), [1.0 + 2.0 ** -7])
+
+
 def pin_round_f16():
     g = synth.rng(38)
     rnd = g.standard_normal(20000) * 10.0 ** g.uniform(-9, 5, 20000)
@@ -583,5 +640,5 @@ PINS = [
     pin_sell_layout_bruteforce, pin_sell_spmv_matches_csr_and_eigen,
     pin_csr_row_bins_bruteforce,
     pin_dense_outer_fd, pin_sampled_outer_fd, pin_scale_dot_gradient,
-    pin_round_bf16, pin_round_f16, pin_round_f32,
+    pin_round_bf16, pin_round_bf16_f64, pin_round_f16, pin_round_f32,
 ]

@@ -51,6 +51,10 @@ MUTANTS = [
     ("scale_operator", "out[i] = s * v[i];", "out[i] = s + v[i];"),
     ("bf16_round_half_up", "if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u))) keep += 1u;",
      "if (rest >= 0x8000u) keep += 1u;"),
+    ("bf16_f64_through_f32", "double r = nearbyint(a / quantum);   /* exact scaling; nearest-even */",
+     "double r = nearbyint((double)(float)a / quantum);"),
+    ("bf16_f64_fraction_bits", "double quantum = (exp_unb < -126) ? ldexp(1.0, -133) : ldexp(1.0, exp_unb - 7);",
+     "double quantum = (exp_unb < -126) ? ldexp(1.0, -133) : ldexp(1.0, exp_unb - 8);"),
     ("f16_subnormal_quantum", "double quantum = (exp_unb < -14) ? ldexp(1.0, -24)",
      "double quantum = (exp_unb < -14) ? ldexp(1.0, -23)"),
     ("f16_widen_bias", "else v = ldexp((double)(1024 + f), e - 25);",
