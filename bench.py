@@ -357,21 +357,140 @@ CPU_SAMPLE_DESC = ("oracle (plain C, FP64 compensated sums, single thread) on a 
                    "Laplacian 32^3 + power-law 50k rows; GB/s from the same algorithmic bytes")
 
 
-def cpu_baseline(min_seconds: float = 10.0):
+CHUNK_ELEMS = 1 << 18       # vector chunk of the all-cores oracle run
+CHUNK_ROWS = 128            # GEMV rows per chunk
+CHUNK_CSR_ROWS = 8192       # CSR rows per chunk
+
+
+def cpu_chunks(items):
+    """The sample split into fixed chunks (independent of the thread count, so
+    every result is the same however many threads run them): a list of
+    (callable, bytes) pairs, each calling the oracle on one chunk."""
+    import numpy as np
+
     import oracle
-    oracle.build()
-    items = cpu_sample_items()
-    cpu_run(items)                               # warm caches / page in
+    out = []
+    for _, _, b, call in items:
+        kind = call[0]
+        if kind in ("copy", "axpy", "dot"):
+            n = call[1].size
+            for a in range(0, n, CHUNK_ELEMS):
+                e = min(n, a + CHUNK_ELEMS)
+                frac = (e - a) / n
+                if kind == "copy":
+                    out.append((lambda y=call[1][a:e]: oracle.copy(y), b * frac))
+                elif kind == "axpy":
+                    out.append((lambda y=call[1][a:e], z=call[2][a:e]: oracle.axpy(y, z, 0.5),
+                                b * frac))
+                else:
+                    out.append((lambda y=call[1][a:e], z=call[2][a:e]: oracle.dot(y, z, True),
+                                b * frac))
+        elif kind == "gemv":
+            _, A, x, g, lay = call
+            for r in range(0, g, CHUNK_ROWS):
+                rows = min(CHUNK_ROWS, g - r)
+                sub = A[r * g:] if lay == "row" else A[r:]
+                out.append((lambda sub=sub, rows=rows, lay=lay, x=x, g=g:
+                            oracle.gemv(sub, x, rows, g, g, lay), b * rows / g))
+        else:
+            _, rp, ci, v, x = call
+            m = rp.size - 1
+            for r in range(0, m, CHUNK_CSR_ROWS):
+                e = min(m, r + CHUNK_CSR_ROWS)
+                lo, hi = int(rp[r]), int(rp[e])
+                srp = (rp[r:e + 1] - lo).astype(np.int32)
+                out.append((lambda srp=srp, c=ci[lo:hi], vv=v[lo:hi], x=x:
+                            oracle.csr_spmv(srp, c, vv, x), b * (e - r) / m))
+    return out
+
+
+def plain_calls(items):
+    """The sample as the plain loops (uncompensated, the data's own precision):
+    (callable, bytes) pairs."""
+    import oracle
+    out = []
+    for _, _, b, call in items:
+        kind = call[0]
+        if kind == "copy":
+            y = call[1]
+            dst = y.copy()
+            out.append((lambda y=y, d=dst: oracle.plain_copy(y, d), b))
+        elif kind == "axpy":
+            y, z = call[1], call[2]
+            dst = y.copy()
+            out.append((lambda y=y, z=z, d=dst: oracle.plain_axpy(y, z, 0.5, d), b))
+        elif kind == "dot":
+            out.append((lambda y=call[1], z=call[2]: oracle.plain_dot(y, z), b))
+        elif kind == "gemv":
+            _, A, x, g, lay = call
+            out.append((lambda A=A, x=x, g=g, lay=lay: oracle.plain_gemv(A, x, g, g, g, lay), b))
+        else:
+            _, rp, ci, v, x = call
+            out.append((lambda rp=rp, ci=ci, v=v, x=x: oracle.plain_csr(rp, ci, v, x), b))
+    return out
+
+
+def _timed_passes(run_pass, min_seconds):
+    run_pass()                                  # warm caches / page in
     t0 = time.perf_counter()
-    total, passes = 0, 0
+    total, passes = 0.0, 0
     while True:
-        total += cpu_run(items)
+        total += run_pass()
         passes += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
-            break
+            return total, passes, el
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def cpu_baseline(min_seconds: float = 10.0):
+    """The oracle on a bounded sample, single-threaded (the reported value),
+    then over every affinitised core on fixed chunks, and the plain
+    uncompensated loops on one core."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    oracle.build()
+    items = cpu_sample_items()
+    total, passes, el = _timed_passes(lambda: cpu_run(items), min_seconds)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    chunks = cpu_chunks(items)
+
+    def parallel_pass(pool):
+        list(pool.map(lambda cb: cb[0](), chunks))
+        return sum(b for _, b in chunks)
+
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        ptotal, ppasses, pel = _timed_passes(lambda: parallel_pass(pool), min_seconds / 4)
+    plain = plain_calls(items)
+
+    def plain_pass():
+        for fn, _ in plain:
+            fn()
+        return sum(b for _, b in plain)
+
+    qtotal, qpasses, qel = _timed_passes(plain_pass, min_seconds / 4)
     return {"value": total / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE_DESC}; {passes} passes in {el:.1f} s"}
+            "sample": f"{CPU_SAMPLE_DESC}; {passes} passes in {el:.1f} s",
+            "all_cores": {"value": ptotal / pel / 1e9, "unit": "GB/s", "cores": cores,
+                          "sample": f"the same oracle calls on fixed chunks ({CHUNK_ELEMS} "
+                                    f"elements, {CHUNK_ROWS} GEMV rows, {CHUNK_CSR_ROWS} CSR "
+                                    f"rows) over {cores} threads; {ppasses} passes in "
+                                    f"{pel:.1f} s"},
+            "plain_loop": {"value": qtotal / qel / 1e9, "unit": "GB/s", "cores": 1,
+                           "sample": f"plain uncompensated loops in the data's precision on "
+                                     f"the same sample; {qpasses} passes in {qel:.1f} s"},
+            "host": host_cpu_model(), "affinity_cores": cores}
 
 
 def run_reference(args):
@@ -424,6 +543,36 @@ def fp64_peak_tflops(sms: int, sm_mhz: float) -> float:
     return sms * 4.0 * sm_mhz * 1e6 / 1e12
 
 
+def fp64_probe(device, stream, iters: int = 10000, reps: int = 3):
+    """The FP64 FMA roof measured live (lak_probe_fma_f64: 8 independent FMA
+    chains per thread, every SM full), median of `reps` launches of ~40 ms
+    timed with events on `stream`, with the SM clock sampled meanwhile."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    sampler = ClockSampler(device.index)
+    sampler.start()
+    time.sleep(0.2)
+    with torch.cuda.stream(stream):
+        out, flops = lak.probe_fma_f64(iters)             # warm-up
+        times = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            lak.probe_fma_f64(iters, out=out)
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+    clocks = sampler.stop()
+    ms = statistics.median(times)
+    tf = flops / (ms * 1e-3) / 1e12
+    mhz = clocks.get("sm_mhz")
+    return {"tflops": tf, "ms_per_launch": ms, "flops_per_launch": flops, "sm_mhz": mhz,
+            "fma_per_sm_per_clk": (tf * 1e12 / 2 / (torch.cuda.get_device_properties(device)
+                                   .multi_processor_count * mhz * 1e6)) if mhz else None,
+            "reasons": clocks.get("reasons")}
+
+
 def flops_of(it) -> float:
     """Algorithmic floating-point operations of one launch (FMA = 2)."""
     if it.op == "axpy":
@@ -452,7 +601,7 @@ def roofline_of(it, ms, hbm_peak, hbm_kind, fp64_peak):
     tf = flops_of(it) / (ms * 1e-3) / 1e12
     alu = {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
            "frac": tf / fp64_peak,
-           "peak_source": "derived: SMs x 4 FP64 flop/clk x median SM clock under load"}
+           "peak_source": "measured: FP64 FMA probe (lak_probe_fma_f64) in this run"}
     return (alu, hbm) if alu["frac"] > hbm["frac"] else (hbm, alu)
 
 
@@ -480,16 +629,11 @@ def run_batched(device, reps=10, count=4096, seed=4000):
     code = _native.DTYPES["f32"]
     fams = {}
 
-    ns = synth.log_uniform_ints(count, 256, 1_048_576, seed)
-    buf_len = int(sum((int(n) + 63) // 64 * 64 for n in ns))
-    ybuf = synth.device_uniform_(torch.empty(buf_len, device=dev), seed + 1)
-    zbuf = synth.device_uniform_(torch.empty(buf_len, device=dev), seed + 2)
-    xbuf = torch.zeros(buf_len, device=dev)
-    ys, zs, xs, o = [], [], [], 0
-    for n in ns:
-        n = int(n)
-        ys.append(ybuf[o:o + n]); zs.append(zbuf[o:o + n]); xs.append(xbuf[o:o + n])
-        o += (n + 63) // 64 * 64
+    wl = synth.batch_workload(dev, count, seed)
+    ys = [v[0] for v in wl["vec"]]
+    zs = [v[1] for v in wl["vec"]]
+    xs = [v[2] for v in wl["vec"]]
+    ns = [y.numel() for y in ys]
     outs = torch.zeros(count, device=dev)
     wsd = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
     fams["axpy"] = (B.axpy_batch(xs, ys, zs, [0.5] * count),
@@ -502,29 +646,20 @@ def run_batched(device, reps=10, count=4096, seed=4000):
                     for i, (y, z) in enumerate(zip(ys, zs))],
                    int(sum(2 * 4 * int(n) for n in ns)))
 
-    ms = synth.log_uniform_ints(count, 64, 4096, seed + 3)
-    nn = synth.log_uniform_ints(count, 64, 4096, seed + 4)
-    As, gx, gy = [], [], []
-    for i, (m, n) in enumerate(zip(ms, nn)):
-        m, n = int(m), int(n)
-        As.append(synth.device_normal_(torch.empty(m, n, device=dev), seed + 10 + i))
-        gx.append(synth.device_uniform_(torch.empty(n, device=dev), seed + 20000 + i))
-        gy.append(torch.zeros(m, device=dev))
+    As = [g[0] for g in wl["gemv"]]
+    gx = [g[1] for g in wl["gemv"]]
+    gy = [g[2] for g in wl["gemv"]]
     fams["gemv"] = (B.gemv_batch(As, gx, gy),
                     [(lib.dense_gemv, (y.data_ptr(), A.data_ptr(), x.data_ptr(), A.shape[0],
                                        A.shape[1], A.shape[1], 0, code, None, 0, None, sh))
                      for A, x, y in zip(As, gx, gy)],
-                    int(sum((int(m) * int(n) + int(m) + int(n)) * 4 for m, n in zip(ms, nn))))
+                    int(sum((A.shape[0] * A.shape[1] + A.shape[0] + A.shape[1]) * 4
+                            for A in As)))
 
-    rows = synth.log_uniform_ints(count, 1000, 200_000, seed + 5)
-    csrs, cx, cy, cbytes = [], [], [], 0
-    for i, m in enumerate(rows):
-        m = int(m)
-        rp, ci, v = synth.device_csr_block_(m, seed + 40000 + i, 5, 64, torch.float32, dev)
-        csrs.append((rp, ci, v, m))
-        cx.append(synth.device_uniform_(torch.empty(m, device=dev), seed + 60000 + i))
-        cy.append(torch.zeros(m, device=dev))
-        cbytes += v.numel() * 8 + (m + 1) * 4 + 2 * m * 4
+    csrs = [c[0] for c in wl["csr"]]
+    cx = [c[1] for c in wl["csr"]]
+    cy = [c[2] for c in wl["csr"]]
+    cbytes = sum(v.numel() * 8 + (m + 1) * 4 + 2 * m * 4 for (_, _, v, m) in csrs)
     fams["spmv"] = (B.spmv_batch(csrs, cx, cy),
                     [(lib.csr_spmv, (y.data_ptr(), rp.data_ptr(), ci.data_ptr(), v.data_ptr(),
                                      x.data_ptr(), m, m, v.numel(), code, None, sh))
@@ -1213,7 +1348,7 @@ def _r(v, nd):
 
 
 def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_step, launches,
-             roofline, per_kernel, e2e, cpu, clocks, detail_path):
+             roofline, per_kernel, e2e, cpu, clocks, detail_path, probe=None):
     """The one JSON line the run ends with: the headline metric and the keys a
     reader needs to check it (roofline of the dominant kernel, per-kernel
     GB/s at the largest sizes, end to end, CPU baseline, clocks), kept within
@@ -1228,6 +1363,8 @@ def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_st
         rl["bytes_per_launch"] = roofline.get("bytes_per_launch")
         rl["flops_per_launch"] = roofline.get("flops_per_launch")
         rl["peak_source"] = str(roofline.get("peak_source", ""))[:80]
+        if roofline.get("peak_nominal") is not None:
+            rl["peak_nominal"] = _r(roofline["peak_nominal"], 4)
         other = roofline.get("other")
         if other:
             rl["other"] = {"bound": other.get("bound"), "unit": other.get("unit"),
@@ -1279,6 +1416,9 @@ def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_st
     }
     if cb is not None:
         line["cpu_baseline"] = cb
+    if probe is not None:
+        line["fp64_probe"] = {"tflops": _r(probe.get("tflops"), 4), "sm_mhz": probe.get("sm_mhz"),
+                              "fma_per_sm_per_clk": _r(probe.get("fma_per_sm_per_clk"), 3)}
     if detail_path:
         line["detail"] = os.path.basename(detail_path)
     return line
@@ -1348,10 +1488,13 @@ def run_gb300(args):
     value = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
 
-    # dominant kernel: largest share of the step time
+    # dominant kernel: largest share of the step time.  The FP64 roof is the
+    # FMA rate measured now (the probe); the unit-count figure is kept beside it
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp64_peak = fp64_peak_tflops(sms, sm_mhz)
+    fp64_nominal = fp64_peak_tflops(sms, sm_mhz)
+    probe = fp64_probe(device, stream)
+    fp64_peak = probe["tflops"]
     dom_name, (dom_it, dom_ms) = max(per.items(), key=lambda kv: kv[1][1])
     bind, other = roofline_of(dom_it, dom_ms, peak, peak_kind, fp64_peak)
     roofline = dict(bind)
@@ -1361,6 +1504,8 @@ def run_gb300(args):
     if other is not None:
         roofline["other"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
     roofline["traffic"] = recorded_traffic(args.traffic_json, dom_it)
+    if roofline["bound"] == "alu":
+        roofline["peak_nominal"] = fp64_nominal
 
     # per (op, dtype) summary at the largest size, and the paper's points.
     # Launches under 100 us are re-timed like the copy and the gather floor
@@ -1474,6 +1619,7 @@ def run_gb300(args):
 
     workload = WORKLOAD if not args.only else f"subset /{args.only}/ of: " + WORKLOAD
     detail = {"per_kernel": summary, "roofline": roofline, "e2e": e2e, "clocks": clocks,
+              "fp64_probe": probe,
               "config": {"workload": workload, "bytes_per_step": bytes_per_step,
                          "launches_per_step": len(items)}}
     for key, val in (("cpu_baseline", cpu), ("precision", precision), ("batched", batched),
@@ -1489,7 +1635,7 @@ def run_gb300(args):
     line = headline(value=value, ms_per_step=ms_per_step, steps=K, warmup=W, world=world,
                     workload=workload, bytes_per_step=bytes_per_step,
                     launches=len(items), roofline=roofline, per_kernel=summary, e2e=e2e,
-                    cpu=cpu, clocks=clocks, detail_path=detail_path)
+                    cpu=cpu, clocks=clocks, detail_path=detail_path, probe=probe)
     if rank == 0:
         print(json.dumps(line, separators=(",", ":")))
     if dist is not None:

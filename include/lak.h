@@ -503,9 +503,11 @@ LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, in
  * the results equal those of the single-instance calls up to the order of
  * floating-point summation (axpy: identical).  The dot keeps at most
  * LAK_WS_COUNTER_BYTES / 4 instances (one arrival counter each).  A NULL cfg
- * (or block 0) takes the batched kernels' own built-in launch shape, not the
- * per-size defaults of the single-instance calls.  Batched GEMV takes at most
- * 128 threads per block (LAK_EINVAL otherwise).
+ * (or block 0) takes the batched default for (op, dtype): the configuration
+ * installed with lak_set_batch_default_cfg (the autotuner's cache), else the
+ * batched kernels' built-in launch shape -- never the per-size defaults of the
+ * single-instance calls.  Batched GEMV takes at most 128 threads per block
+ * (LAK_EINVAL otherwise).
  * ---------------------------------------------------------------------- */
 typedef struct { void *x; const void *y; const void *z; int64_t n; double alpha; } lak_axpy_desc;
 typedef struct { void *out; const void *x; const void *y; int64_t n; } lak_dot_desc;
@@ -532,6 +534,37 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
 
 LAK_API lak_status lak_batch_run(const lak_batch_info *info, const void *dev_table, void *workspace,
                                  size_t ws_bytes, void *stream);
+
+/*
+ * Default launch configuration of lak_batch_plan for (op, dtype) when it is
+ * given no cfg (the batched form of Sec. 2's tuning parameters, chosen by this
+ * library's autotuner over the batching workload).  cfg = NULL or block 0
+ * removes the entry (back to the built-in shape).  block: 32..512 in steps of
+ * 32 (batched GEMV: at most 128); grid >= 0 (0 = as many blocks as fit on the
+ * device at once); vec 0 (the built-in width) or 1, 2, 4, 8, 16 (CSR uses 4 or
+ * 8 entries per lane and clamps to that range).  Host only; process-wide;
+ * plans made earlier keep their configuration.
+ */
+LAK_API lak_status lak_set_batch_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg);
+
+/* ------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper, whose roofs are the devices'
+ * nominal memory bandwidths, Sec. 3): the FP64 FMA throughput of the device.
+ * On GB300 the FP64 dense and sparse products are bound by the FP64 pipe, so
+ * their roof is this measured rate.
+ *
+ * lak_probe_fma_f64 launches `grid` blocks of `block` threads; every thread
+ * runs 8 independent chains of `iters` dependent FMAs (a <- a*b + c with
+ * values that stay normal), then the chains are summed and reduced over each
+ * warp and lane 0 writes one double to out[warp index], so `out` (device) must
+ * hold grid * block / 32 doubles.  lak_probe_fma_f64_flops gives the floating-
+ * point operations of such a launch (2 per FMA).  Time it with events on
+ * `stream`.  Errors: LAK_EINVAL for iters < 1, grid < 1, block outside
+ * 32..1024 or not a multiple of 32, or a NULL / misaligned out.
+ * ---------------------------------------------------------------------- */
+LAK_API lak_status lak_probe_fma_f64(double *out, int64_t iters, int32_t grid, int32_t block,
+                                     void *stream);
+LAK_API int64_t lak_probe_fma_f64_flops(int64_t iters, int32_t grid, int32_t block);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,9 @@ Functions and the passages they follow (Rupp et al., IWOCL'14):
   csr_to_csc, dense_outer,
   sampled_outer, scale ..... reverse-mode derivatives of the products above
   round_bf16 / round_f16 ... reduced-precision storage of the same data
+  plain_* .................. NOT reference values: uncompensated FP32/FP64
+                             loops that the benchmark times as the "plain CPU"
+                             baseline beside the oracle
 """
 from __future__ import annotations
 
@@ -89,7 +92,13 @@ def _bind(path: str):
         "orc_csr_to_sell": (_I64, [_I32P, _I32P, _I64, _I64, _I64, _I32P, _I32P, _I64P, _I32P,
                                    _I32P]),
         "orc_sell_spmv": (None, [_F64P, _I64, _I64, _I32P, _I32P, _I64P, _I32P, _F64P, _F64P]),
+        "orc_plain_copy": (None, [ctypes.c_void_p, ctypes.c_void_p, _I64]),
     }
+    for suf, fp, ct in (("f32", _F32P, ctypes.c_float), ("f64", _F64P, ctypes.c_double)):
+        sig[f"orc_plain_axpy_{suf}"] = (None, [fp, fp, fp, ct, _I64])
+        sig[f"orc_plain_dot_{suf}"] = (ctypes.c_double, [fp, fp, _I64])
+        sig[f"orc_plain_gemv_{suf}"] = (None, [fp, fp, fp, _I64, _I64, _I64, ctypes.c_int])
+        sig[f"orc_plain_csr_{suf}"] = (None, [fp, _I32P, _I32P, fp, fp, _I64])
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -380,3 +389,45 @@ def round_to(v, storage: str) -> np.ndarray:
     if storage == "f16":
         return widen_f16_bits(round_f16(v))
     raise ValueError(storage)
+
+
+# ---- plain loops (the "plain CPU" baseline; not reference values) ---------------
+
+def plain_axpy(y, z, alpha: float, out=None):
+    """x = y + alpha z in the inputs' own precision (float32 or float64 arrays)."""
+    suf = "f32" if y.dtype == np.float32 else "f64"
+    x = np.empty_like(y) if out is None else out
+    fp = _F32P if suf == "f32" else _F64P
+    getattr(_load(), f"orc_plain_axpy_{suf}")(_ptr(x, fp), _ptr(y, fp), _ptr(z, fp), alpha, y.size)
+    return x
+
+
+def plain_dot(x, y) -> float:
+    suf = "f32" if x.dtype == np.float32 else "f64"
+    fp = _F32P if suf == "f32" else _F64P
+    return getattr(_load(), f"orc_plain_dot_{suf}")(_ptr(x, fp), _ptr(y, fp), x.size)
+
+
+def plain_gemv(A, x, m: int, n: int, lda: int, layout: str = "row", out=None):
+    suf = "f32" if A.dtype == np.float32 else "f64"
+    fp = _F32P if suf == "f32" else _F64P
+    y = np.empty(m, A.dtype) if out is None else out
+    getattr(_load(), f"orc_plain_gemv_{suf}")(_ptr(y, fp), _ptr(A, fp), _ptr(x, fp), m, n, lda,
+                                              {"row": 0, "col": 1}[layout])
+    return y
+
+
+def plain_csr(row_ptr, col_idx, vals, x, out=None):
+    suf = "f32" if vals.dtype == np.float32 else "f64"
+    fp = _F32P if suf == "f32" else _F64P
+    m = row_ptr.size - 1
+    y = np.empty(m, vals.dtype) if out is None else out
+    getattr(_load(), f"orc_plain_csr_{suf}")(_ptr(y, fp), _ptr(row_ptr, _I32P),
+                                             _ptr(col_idx, _I32P), _ptr(vals, fp), _ptr(x, fp), m)
+    return y
+
+
+def plain_copy(y, out=None):
+    x = np.empty_like(y) if out is None else out
+    _load().orc_plain_copy(x.ctypes.data, y.ctypes.data, y.nbytes)
+    return x

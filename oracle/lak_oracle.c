@@ -502,3 +502,55 @@ void orc_round_f32(float *out, const double *in, int64_t n)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = (float)in[i];
 }
+
+/* ---- plain loops: the "plain CPU" baseline, not reference values ----------
+ *
+ * The benchmark times these beside the oracle: the same operations as the
+ * straightforward loops a CPU programmer would write, in the storage type's own
+ * arithmetic (FP32 sums for FP32 data), with no compensation.  Nothing checks a
+ * kernel against them; a CPU test checks them against the oracle above.
+ */
+#define ORC_PLAIN(T, SUF)                                                          \
+void orc_plain_axpy_##SUF(T *x, const T *y, const T *z, T alpha, int64_t n)        \
+{                                                                                  \
+    for (int64_t i = 0; i < n; ++i) x[i] = y[i] + alpha * z[i];                   \
+}                                                                                  \
+double orc_plain_dot_##SUF(const T *x, const T *y, int64_t n)                      \
+{                                                                                  \
+    T s = 0;                                                                       \
+    for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];                              \
+    return (double)s;                                                              \
+}                                                                                  \
+void orc_plain_gemv_##SUF(T *y, const T *A, const T *x, int64_t m, int64_t n,      \
+                          int64_t lda, int layout)                                 \
+{                                                                                  \
+    if (layout == 0) {                                                             \
+        for (int64_t i = 0; i < m; ++i) {                                          \
+            T s = 0;                                                               \
+            for (int64_t j = 0; j < n; ++j) s += A[i * lda + j] * x[j];            \
+            y[i] = s;                                                              \
+        }                                                                          \
+    } else {                                                                       \
+        for (int64_t i = 0; i < m; ++i) y[i] = 0;                                  \
+        for (int64_t j = 0; j < n; ++j)                                            \
+            for (int64_t i = 0; i < m; ++i) y[i] += A[i + j * lda] * x[j];         \
+    }                                                                              \
+}                                                                                  \
+void orc_plain_csr_##SUF(T *y, const int32_t *row_ptr, const int32_t *col_idx,     \
+                         const T *vals, const T *x, int64_t m)                     \
+{                                                                                  \
+    for (int64_t i = 0; i < m; ++i) {                                              \
+        T s = 0;                                                                   \
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)                      \
+            s += vals[k] * x[col_idx[k]];                                          \
+        y[i] = s;                                                                  \
+    }                                                                              \
+}
+
+ORC_PLAIN(float, f32)
+ORC_PLAIN(double, f64)
+
+void orc_plain_copy(void *dst, const void *src, int64_t nbytes)
+{
+    memcpy(dst, src, (size_t)nbytes);
+}

@@ -29,7 +29,7 @@ __all__ = ["vec_copy", "vec_axpy", "vec_axpby", "vec_axpy_norm2", "vec_axpy_norm
            "vec_dot_noalloc", "dense_gemv",
            "dense_gemv_workspace", "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose", "vec_gather", "vec_scale_dev", "resolve_cfg", "set_default_cfg",
-           "size_bucket", "SIZE_BUCKETS", "Cfg",
+           "size_bucket", "SIZE_BUCKETS", "Cfg", "set_batch_default_cfg", "probe_fma_f64",
            "LakError", "storage_of", "library_path"]
 
 _lib = _native.load()
@@ -175,6 +175,30 @@ def set_default_cfg(op: str, storage: str, cfg: CfgLike, bucket: Optional[int] =
     _native.check("lak_set_default_cfg",
                   _lib.lak_set_default_cfg_bucket(OPS[op], DTYPES[storage], b, _cfg_ptr(cfg)))
     _dot_ws_sizes.clear()                 # workspace needs follow the defaults
+
+
+def set_batch_default_cfg(op: str, storage: str, cfg: CfgLike):
+    """Replace (or with cfg=None restore) the launch configuration that
+    batched launches of `op` take when planned without one."""
+    _native.check("lak_set_batch_default_cfg",
+                  _lib.lak_set_batch_default_cfg(OPS[op], DTYPES[storage], _cfg_ptr(cfg)))
+
+
+def probe_fma_f64(iters: int, grid: Optional[int] = None, block: int = 256,
+                  out: Optional[torch.Tensor] = None, stream=None):
+    """Launch the FP64 FMA throughput probe (lak_probe_fma_f64) on the current
+    device; grid defaults to as many blocks as are resident at once.  Returns
+    (out, flops of the launch)."""
+    if grid is None:
+        p = torch.cuda.get_device_properties(_current_device())
+        grid = p.multi_processor_count * (p.max_threads_per_multi_processor // block)
+    if out is None:
+        out = torch.empty(grid * block // 32, dtype=torch.float64,
+                          device=torch.device("cuda", _current_device()))
+    st = _lib.lak_probe_fma_f64(_dev_ptr(out, "out"), int(iters), int(grid), int(block),
+                                _stream(stream))
+    _native.check("lak_probe_fma_f64", st)
+    return out, int(_lib.lak_probe_fma_f64_flops(int(iters), int(grid), int(block)))
 
 
 # vec_dot_workspace(n, storage) for calls without an explicit cfg, memoised

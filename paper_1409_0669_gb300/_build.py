@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblak_gb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["lak_api.cu", "k_vec.cu", "k_gemv.cu", "k_spmv.cu", "k_dot_noalloc.cu", "k_batch.cu", "k_grad.cu", "k_vec_ext.cu", "k_sell.cu", "k_csr_bin.cu"]
+SOURCES = ["lak_api.cu", "k_vec.cu", "k_gemv.cu", "k_spmv.cu", "k_dot_noalloc.cu", "k_batch.cu", "k_grad.cu", "k_vec_ext.cu", "k_sell.cu", "k_csr_bin.cu", "k_probe.cu"]
 
 
 def nvcc_path() -> str:

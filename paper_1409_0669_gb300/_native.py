@@ -32,7 +32,8 @@ EXPORTS = ("lak_last_error", "lak_abi_version", "lak_set_default_cfg", "lak_reso
            "csr_spmv", "dense_outer", "csr_sampled_outer",
            "csr_transpose_workspace", "csr_transpose", "vec_gather", "vec_scale_dev",
            "csr_to_sell_count", "csr_to_sell_fill", "sell_pack_values", "sell_spmv",
-           "lak_batch_plan", "lak_batch_run")
+           "lak_batch_plan", "lak_batch_run", "lak_set_batch_default_cfg", "lak_probe_fma_f64",
+           "lak_probe_fma_f64_flops")
 
 
 class LakCfg(ctypes.Structure):
@@ -128,6 +129,9 @@ _SIGNATURES = {
     "sell_spmv": (_I32, [_P, _P, _P, _P, _P, _P, _P, _I64, _I32, _CFGP, _P]),
     "lak_batch_plan": (_I32, [_I32, _I32, _P, _I64, _CFGP, _P, _SZ, ctypes.POINTER(BatchInfo)]),
     "lak_batch_run": (_I32, [ctypes.POINTER(BatchInfo), _P, _P, _SZ, _P]),
+    "lak_set_batch_default_cfg": (_I32, [_I32, _I32, _CFGP]),
+    "lak_probe_fma_f64": (_I32, [_P, _I64, _I32, _I32, _P]),
+    "lak_probe_fma_f64_flops": (_I64, [_I64, _I32, _I32]),
 }
 
 _lib = None

@@ -25,13 +25,25 @@ tune the copy kernel exhaustively, keep the configurations within 15 % of the
 best copy, and measure how close the best of those comes to each other
 operation's own optimum.
 
+The batched persistent launches (lak_batch_plan / lak_batch_run) have their
+own space -- block 32..512 (batched GEMV: up to 128), grid automatic or 1..16
+blocks per SM, 2..16 elements per access (CSR: 4 or 8 entries per lane), both
+increments (the CSR batch schedules dynamically, so only one) -- searched by
+`tune_batch` on the batching workload itself (4096 uneven instances of one
+family, synth.batch_workload), one run of the whole batch per timing.
+
 The winners can be saved as a JSON cache keyed by GPU name and SM count and
-installed as the library's per-op defaults (lak_set_default_cfg).
+installed as the library's per-op defaults (lak_set_default_cfg;
+"batch:<op>:<storage>" entries: lak_set_batch_default_cfg).  The cache this
+package ships (tuned_defaults.json) holds the batched defaults measured on
+GB300; the batched runner installs it for a matching GPU on first use.
 
   python -m paper_1409_0669_gb300.autotune --op copy --storage f32 --size 100000000
   python -m paper_1409_0669_gb300.autotune --study --storage f32 --out tune.json
   python -m paper_1409_0669_gb300.autotune --buckets --op dot --storage f64 \
       --size 46416,215443,2154435,10000000 --out tune.json
+  python -m paper_1409_0669_gb300.autotune --batch --op gemv_row --storage f32 \
+      --out tune.json --save-cache paper_1409_0669_gb300/tuned_defaults.json
 """
 from __future__ import annotations
 
@@ -236,6 +248,106 @@ def copy_first_study(storage: str, sizes: Dict[str, object], keep_frac: float = 
     return report
 
 
+# ---- batched launches -------------------------------------------------------------
+
+BATCH_OPS = ("axpy", "dot", "gemv_row", "spmv")
+BATCH_GRID_PER_SM = (0, 1, 2, 4, 8, 16)          # 0 = as many blocks as fit at once
+
+
+def batch_space(op: str, sms: int) -> List[LakCfg]:
+    """Launch configurations of one batched family."""
+    blocks = (32, 64, 128) if op == "gemv_row" else (32, 64, 128, 256, 512)
+    vecs = (4, 8) if op == "spmv" else (2, 4, 8, 16)
+    incs = (0,) if op == "spmv" else (0, 1)
+    return [LakCfg(b, k * sms, v, inc) for inc in incs for v in vecs for b in blocks
+            for k in BATCH_GRID_PER_SM]
+
+
+class BatchProblem:
+    """One family of the batching workload (4096 uneven instances) on the
+    current device; time_cfg plans the batch with a configuration and times
+    one persistent launch over all instances."""
+
+    def __init__(self, op: str, storage: str, count: int = 4096, seed: int = 4000, device=None):
+        import synth
+        if op not in BATCH_OPS:
+            raise ValueError(op)
+        self.op, self.storage, self.count = op, storage, count
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream(self.device)
+        fam = {"axpy": "vec", "dot": "vec", "gemv_row": "gemv", "spmv": "csr"}[op]
+        wl = synth.batch_workload(self.device, count, seed, synth.torch_dtype(storage),
+                                  families=(fam,))
+        es = torch.tensor([], dtype=synth.torch_dtype(storage)).element_size()
+        self.keep = wl
+        if op in ("axpy", "dot"):
+            n = sum(v[0].numel() for v in wl["vec"])
+            self.nbytes = (3 if op == "axpy" else 2) * n * es
+            self.outs = torch.zeros(count, dtype=torch.float64 if storage == "f64"
+                                    else torch.float32, device=self.device)
+        elif op == "gemv_row":
+            self.nbytes = sum((A.numel() + A.shape[0] + A.shape[1]) * es
+                              for A, _, _ in wl["gemv"])
+        else:
+            self.nbytes = sum(v.numel() * (es + 4) + (m + 1) * 4 + 2 * m * es
+                              for (_, _, v, m), _, _ in wl["csr"])
+
+    def batch(self, cfg: Optional[LakCfg]):
+        from . import batch as B
+        wl = self.keep
+        c = None if cfg is None else tuple(cfg.as_tuple())
+        if self.op == "axpy":
+            return B.axpy_batch([v[2] for v in wl["vec"]], [v[0] for v in wl["vec"]],
+                                [v[1] for v in wl["vec"]], [0.5] * self.count, cfg=c)
+        if self.op == "dot":
+            return B.dot_batch([v[0] for v in wl["vec"]], [v[1] for v in wl["vec"]],
+                               [self.outs[i:i + 1] for i in range(self.count)], cfg=c)
+        if self.op == "gemv_row":
+            return B.gemv_batch([g[0] for g in wl["gemv"]], [g[1] for g in wl["gemv"]],
+                                [g[2] for g in wl["gemv"]], cfg=c)
+        return B.spmv_batch([g[0] for g in wl["csr"]], [g[1] for g in wl["csr"]],
+                            [g[2] for g in wl["csr"]], cfg=c)
+
+    def time_cfg(self, cfg: Optional[LakCfg], reps: int = 5) -> float:
+        """Device time of one run of the whole batch in microseconds (median
+        of `reps` launches, each bracketed by events on the stream).  The
+        batch reads ~1-70 GB, far more than L2 holds."""
+        b = self.batch(cfg)
+        b.run(self.stream)
+        torch.cuda.synchronize(self.device)
+        times = []
+        for _ in range(reps):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(self.stream)
+            b.run(self.stream)
+            e.record(self.stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e) * 1e3)
+        times.sort()
+        return times[len(times) // 2]
+
+
+def tune_batch(op: str, storage: str, count: int = 4096, reps: int = 5,
+               cfgs: Optional[List[LakCfg]] = None,
+               problem: Optional[BatchProblem] = None) -> List[Dict]:
+    """Time every batched configuration of one family; fastest first (each
+    entry: cfg, us, GB/s).  The built-in default is timed too (cfg None)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    prob = problem or BatchProblem(op, storage, count, device=dev)
+    results = []
+    for c in (cfgs if cfgs is not None else batch_space(op, sms)):
+        try:
+            us = prob.time_cfg(c, reps)
+        except LakError:
+            continue
+        results.append({"cfg": list(c.as_tuple()), "us": us,
+                        "GBs": prob.nbytes / (max(us, 1e-3) * 1e-6) / 1e9})
+    results.sort(key=lambda r: r["us"])
+    return results
+
+
 def problem_bucket(prob: Problem) -> int:
     """Size bucket of a Problem's call (lak_size_bucket)."""
     lib = _native.load()
@@ -296,17 +408,25 @@ def save_cache(path: str, entries: Dict[str, List[int]]):
         json.dump(data, fh, indent=1, sort_keys=True)
 
 
-def apply_cache(path: str) -> int:
-    """Install the cached configurations for this GPU as library defaults."""
-    from . import set_default_cfg
+def apply_cache(path: str, only_batch: bool = False) -> int:
+    """Install the cached configurations for this GPU as library defaults
+    ("batch:<op>:<storage>" entries as batched defaults); returns how many."""
+    from . import set_batch_default_cfg, set_default_cfg
     with open(path) as fh:
         data = json.load(fh)
     entries = data.get(cache_key(), {})
+    done = 0
     for key, cfg in entries.items():
         parts = key.split(":")
-        bucket = int(parts[2]) if len(parts) == 3 else None
-        set_default_cfg(parts[0], parts[1], tuple(cfg), bucket)
-    return len(entries)
+        if parts[0] == "batch":
+            set_batch_default_cfg(parts[1], parts[2], tuple(cfg))
+        elif only_batch:
+            continue
+        else:
+            bucket = int(parts[2]) if len(parts) == 3 else None
+            set_default_cfg(parts[0], parts[1], tuple(cfg), bucket)
+        done += 1
+    return done
 
 
 def _main(argv=None):
@@ -321,12 +441,27 @@ def _main(argv=None):
                     help="run the study at the paper's sizes (2e6-entry vectors, 2048^2)")
     ap.add_argument("--buckets", action="store_true",
                     help="one configuration per size bucket from the comma-separated --size list")
+    ap.add_argument("--batch", action="store_true",
+                    help="tune the batched launch of --op on the batching workload")
+    ap.add_argument("--count", type=int, default=4096, help="instances of a --batch family")
+    ap.add_argument("--save-cache", default=None,
+                    help="merge the winner(s) into this JSON cache under this GPU's key")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     size = args.size
     if size.isdigit():
         size = int(size)
-    if args.buckets:
+    cache_entries = {}
+    if args.batch:
+        res = tune_batch(args.op, args.storage, args.count, reps=min(args.reps, 5))
+        prob_default = BatchProblem(args.op, args.storage, args.count)
+        default_us = prob_default.time_cfg(None)
+        del prob_default
+        cache_entries[f"batch:{args.op}:{args.storage}"] = res[0]["cfg"]
+        text = json.dumps({"op": args.op, "storage": args.storage, "count": args.count,
+                           "top": res[:args.top], "worst": res[-3:], "count_cfgs": len(res),
+                           "builtin_default_us": default_us}, indent=1)
+    elif args.buckets:
         sizes = [int(v) if v.isdigit() else v for v in args.size.split(",")]
         per = tune_buckets(args.op, args.storage, sizes, args.reps)
         text = json.dumps({"op": args.op, "storage": args.storage,
@@ -353,6 +488,8 @@ def _main(argv=None):
     if args.out:
         with open(args.out, "w") as fh:
             fh.write(text)
+    if args.save_cache and cache_entries:
+        save_cache(args.save_cache, cache_entries)
 
 
 if __name__ == "__main__":

@@ -10,6 +10,7 @@ while it is used.
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Optional, Sequence
 
 import torch
@@ -27,6 +28,25 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
     return _dev_ptr(t, "batched operand")
 
 
+TUNED_DEFAULTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_defaults.json")
+_installed = set()
+
+
+def install_tuned_defaults(path: str = TUNED_DEFAULTS) -> int:
+    """Install the batched launch defaults the autotuner measured for this GPU
+    model (its "batch:<op>:<storage>" entries; other GPUs keep the built-in
+    shapes).  Runs once per device per process, on the first batch planned
+    there; returns the number of entries installed."""
+    dev = torch.cuda.current_device()
+    if dev in _installed:
+        return 0
+    _installed.add(dev)
+    if not os.path.exists(path):
+        return 0
+    from .autotune import apply_cache
+    return apply_cache(path, only_batch=True)
+
+
 def _cfg(cfg):
     if cfg is None:
         return None
@@ -37,6 +57,7 @@ def _cfg(cfg):
 class Batch:
     def __init__(self, op: str, storage: str, descs, cfg=None, device=None, keep=()):
         lib = _native.load()
+        install_tuned_defaults()
         self.op, self.storage = op, storage
         count = len(descs)
         arr_t = type(descs[0]) * count if count else AxpyDesc * 0

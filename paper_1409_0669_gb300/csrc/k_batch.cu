@@ -218,7 +218,6 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // values to L1 but keeps twice the blocks -- and with them twice the loads --
 // in flight (4.0 vs 3.5 TB/s on the 2048-instance mix; the batched GEMV is
 // latency-bound, not arithmetic-bound).
-constexpr int kGemvBatchMaxBlock = 128;
 
 template <typename T, int V>
 __global__ void __launch_bounds__(kGemvBatchMaxBlock, 8)

@@ -218,6 +218,21 @@ lak_cfg g_override[LAK_OP_COUNT][4][LAK_SIZE_BUCKETS];
 bool g_has_override[LAK_OP_COUNT][4][LAK_SIZE_BUCKETS];
 std::mutex g_cfg_mu;
 
+// Batched defaults installed with lak_set_batch_default_cfg (axpy, dot,
+// row-major GEMV, CSR), per storage type.
+lak_cfg g_batch_override[4][4];
+bool g_has_batch_override[4][4];
+
+int batch_op_index(lak_op op) {
+    switch (op) {
+    case LAK_OP_AXPY: return 0;
+    case LAK_OP_DOT: return 1;
+    case LAK_OP_GEMV_ROW: return 2;
+    case LAK_OP_SPMV: return 3;
+    default: return -1;
+    }
+}
+
 bool valid_dtype(lak_dtype dt) { return dt == LAK_F32 || dt == LAK_F64 || dt == LAK_BF16 || dt == LAK_F16; }
 bool valid_op(lak_op op) { return op >= 0 && op < LAK_OP_COUNT; }
 bool pow2_vec(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; }
@@ -446,7 +461,14 @@ lak_status plan_spmv(lak_dtype dt, int64_t m, int64_t n, int64_t nnz, const lak_
 
 lak_cfg batch_config(lak_op op, lak_dtype dt, const lak_cfg *cfg) {
     const BatchCfg b = batch_row(op, dt);
-    lak_cfg c = (cfg && cfg->block != 0) ? *cfg : lak_cfg{b.block, 0, 0, b.inc};
+    lak_cfg c{b.block, 0, 0, b.inc};
+    if (cfg && cfg->block != 0) {
+        c = *cfg;
+    } else {
+        std::lock_guard<std::mutex> lk(g_cfg_mu);
+        const int bi = batch_op_index(op);
+        if (bi >= 0 && g_has_batch_override[bi][dt]) c = g_batch_override[bi][dt];
+    }
     if (c.vec == 0) c.vec = op == LAK_OP_SPMV ? 4 : vec_for_bytes(b.bytes, esize(dt));
     return c;
 }
@@ -528,6 +550,25 @@ LAK_API lak_status lak_set_default_cfg_bucket(lak_op op, lak_dtype dtype, int32_
 
 LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg) {
     return lak_set_default_cfg_bucket(op, dtype, -1, cfg);
+}
+
+LAK_API lak_status lak_set_batch_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg) {
+    const int bi = batch_op_index(op);
+    if (bi < 0) return fail(LAK_EINVAL, "lak_set_batch_default_cfg: op %d has no batched form", (int)op);
+    if (!valid_dtype(dtype))
+        return fail(LAK_EDTYPE, "lak_set_batch_default_cfg: unknown dtype %d", (int)dtype);
+    if (cfg && cfg->block != 0) {
+        const int max_block = op == LAK_OP_GEMV_ROW ? kGemvBatchMaxBlock : 512;
+        if (cfg->block < 32 || cfg->block > max_block || cfg->block % 32 || cfg->grid < 0 ||
+            (cfg->vec != 0 && !pow2_vec(cfg->vec)) ||
+            (cfg->increment != LAK_INC_GLOBAL && cfg->increment != LAK_INC_LOCAL))
+            return fail(LAK_EINVAL, "lak_set_batch_default_cfg: invalid cfg (%d, %d, %d, %d)",
+                        cfg->block, cfg->grid, cfg->vec, cfg->increment);
+    }
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_has_batch_override[bi][dtype] = cfg && cfg->block != 0;
+    if (g_has_batch_override[bi][dtype]) g_batch_override[bi][dtype] = *cfg;
+    return LAK_OK;
 }
 
 LAK_API int32_t lak_size_bucket(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz) {

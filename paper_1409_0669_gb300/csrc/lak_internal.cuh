@@ -95,6 +95,9 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
 }
 
+// Largest block of the batched GEMV kernel (its register budget is set for it).
+constexpr int kGemvBatchMaxBlock = 128;
+
 // The configuration a batched launch starts from (explicit cfg, else the
 // batched kernels' own defaults), with vec filled in; host only, no CUDA
 // call; grid left as given.

@@ -275,3 +275,65 @@ def device_csr_block_(m: int, seed: int, min_len: int, max_len: int, dtype, devi
     ci = torch.randint(0, m, (nnz,), generator=g, device=device, dtype=torch.int32)
     v = torch.empty(nnz, dtype=torch.float32, device=device).normal_(0.0, 1.0, generator=g)
     return rp, ci, v.to(dtype)
+
+
+def batch_workload(device, count: int = 4096, seed: int = 4000, dtype=torch.float32,
+                   families=("vec", "gemv", "csr")):
+    """The batching workload's instances, drawn on the device: `count` uneven
+    instances per family.
+      vectors: n log-uniform in [256, 1,048,576]; y, z ~ U(-1, 1), x zeroed
+        (slices of three flat buffers, each slice starting on a 64-element
+        boundary);
+      dense GEMV: m, n independently log-uniform in [64, 4096], A ~ N(0, 1)
+        row-major, x ~ U(-1, 1), y zeroed;
+      CSR: square blocks of m log-uniform in [1,000, 200,000] rows with 5..64
+        entries per row (device_csr_block_), x ~ U(-1, 1), y zeroed.
+    Returns {"vec": [(y, z, x)], "gemv": [(A, x, y)], "csr": [((rp, ci, v, m), x, y)]},
+    with only the requested families drawn (each family's draws do not depend
+    on which others are requested)."""
+    out = {}
+    if "vec" in families:
+        out["vec"] = _batch_vectors(device, count, seed, dtype)
+    if "gemv" in families:
+        out["gemv"] = _batch_gemv(device, count, seed, dtype)
+    if "csr" in families:
+        out["csr"] = _batch_csr(device, count, seed, dtype)
+    return out
+
+
+def _batch_vectors(device, count, seed, dtype):
+    ns = log_uniform_ints(count, 256, 1_048_576, seed)
+    buf_len = int(sum((int(n) + 63) // 64 * 64 for n in ns))
+    ybuf = device_uniform_(torch.empty(buf_len, dtype=dtype, device=device), seed + 1)
+    zbuf = device_uniform_(torch.empty(buf_len, dtype=dtype, device=device), seed + 2)
+    xbuf = torch.zeros(buf_len, dtype=dtype, device=device)
+    vec, o = [], 0
+    for n in ns:
+        n = int(n)
+        vec.append((ybuf[o:o + n], zbuf[o:o + n], xbuf[o:o + n]))
+        o += (n + 63) // 64 * 64
+    return vec
+
+
+def _batch_gemv(device, count, seed, dtype):
+    ms = log_uniform_ints(count, 64, 4096, seed + 3)
+    nn = log_uniform_ints(count, 64, 4096, seed + 4)
+    gemv = []
+    for i, (m, n) in enumerate(zip(ms, nn)):
+        m, n = int(m), int(n)
+        gemv.append((device_normal_(torch.empty(m, n, dtype=dtype, device=device), seed + 10 + i),
+                     device_uniform_(torch.empty(n, dtype=dtype, device=device), seed + 20000 + i),
+                     torch.zeros(m, dtype=dtype, device=device)))
+    return gemv
+
+
+def _batch_csr(device, count, seed, dtype):
+    rows = log_uniform_ints(count, 1000, 200_000, seed + 5)
+    csr = []
+    for i, m in enumerate(rows):
+        m = int(m)
+        rp, ci, v = device_csr_block_(m, seed + 40000 + i, 5, 64, dtype, device)
+        csr.append(((rp, ci, v, m),
+                    device_uniform_(torch.empty(m, dtype=dtype, device=device), seed + 60000 + i),
+                    torch.zeros(m, dtype=dtype, device=device)))
+    return csr

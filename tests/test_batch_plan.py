@@ -83,3 +83,39 @@ def test_plan_rejects_bad_input(nat):
     assert lib.lak_batch_plan(nat.OPS["dot"], 0, many, 20000, None, None, 0,
                               ctypes.byref(info)) == -1
     assert "dot instances" in nat.last_error()
+
+
+def test_batch_default_cfg_comes_from_the_installed_entry(nat, tmp_path, monkeypatch):
+    """A plan without a cfg takes the entry installed with
+    lak_set_batch_default_cfg (as the autotuner's cache installs it), falls back
+    to the built-in shape when the entry is removed, and an explicit cfg still
+    wins; invalid entries are refused."""
+    lib = nat.load()
+    g = [nat.GemvDesc(256, 512, 768, 100, 1000, 1000)]
+    builtin = plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple()
+    try:
+        tuned = nat.LakCfg(96, 152 * 4, 4, 1)
+        assert lib.lak_set_batch_default_cfg(nat.OPS["gemv_row"], nat.DTYPES["f32"],
+                                             ctypes.byref(tuned)) == 0
+        assert plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple() == (96, 608, 4, 1)
+        # other storage types and ops keep their own defaults
+        assert plan(nat, "gemv_row", "f64", g)[0].cfg.as_tuple() != (96, 608, 4, 1)
+        explicit = nat.LakCfg(64, 0, 8, 0)
+        assert plan(nat, "gemv_row", "f32", g, explicit)[0].cfg.as_tuple() == (64, 0, 8, 0)
+        for bad in (nat.LakCfg(256, 0, 4, 0), nat.LakCfg(48, 0, 4, 0), nat.LakCfg(64, -1, 4, 0),
+                    nat.LakCfg(64, 0, 3, 0), nat.LakCfg(64, 0, 4, 2)):
+            assert lib.lak_set_batch_default_cfg(nat.OPS["gemv_row"], nat.DTYPES["f32"],
+                                                 ctypes.byref(bad)) == nat.LAK_EINVAL
+        assert lib.lak_set_batch_default_cfg(nat.OPS["copy"], 0, None) == nat.LAK_EINVAL
+        # the autotuner's cache file format, installed through apply_cache
+        import json
+        from paper_1409_0669_gb300 import autotune
+        monkeypatch.setattr(autotune, "cache_key", lambda: "TEST GPU|sms=152")
+        path = tmp_path / "cache.json"
+        path.write_text(json.dumps({"TEST GPU|sms=152": {"batch:gemv_row:f32": [32, 0, 8, 0]},
+                                    "OTHER|sms=1": {"batch:gemv_row:f32": [128, 0, 2, 0]}}))
+        assert autotune.apply_cache(str(path), only_batch=True) == 1
+        assert plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple() == (32, 0, 8, 0)
+    finally:
+        assert lib.lak_set_batch_default_cfg(nat.OPS["gemv_row"], nat.DTYPES["f32"], None) == 0
+    assert plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple() == builtin

@@ -167,6 +167,7 @@ def _fake_run_parts(bench):
             "ms_per_launch": 0.46271234567,
             "peak_source": "measured: FP64 FMA probe (independent chains) x SMs at the "
                            "median SM clock under load, and more words to be cut",
+            "peak_nominal": 1.2586012345,
             "other": {"bound": "hbm", "achieved": 4641.123456, "peak": 6785.9, "unit": "GB/s",
                       "frac": 0.683987654}}
     e2e = {"value": 349.987654321, "unit": "GB/s", "h2d_bytes_per_step": 14123456789,
@@ -192,7 +193,9 @@ def test_headline_is_compact_and_complete():
     line = bench.headline(value=5266.123456789, ms_per_step=4.8123456789, steps=20, warmup=5,
                           world=1, workload=bench.WORKLOAD, bytes_per_step=25312345678,
                           launches=124, roofline=roof, per_kernel=per, e2e=e2e, cpu=cpu,
-                          clocks=clocks, detail_path="/some/where/bench_detail.json")
+                          clocks=clocks, detail_path="/some/where/bench_detail.json",
+                          probe={"tflops": 1.2345678901, "sm_mhz": 2070.0,
+                                 "fma_per_sm_per_clk": 1.9612345, "ms_per_launch": 40.1234})
     text = json.dumps(line, separators=(",", ":"))
     assert len(text.encode()) <= bench.HEADLINE_MAX_BYTES, len(text)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
