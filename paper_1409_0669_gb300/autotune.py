@@ -39,7 +39,9 @@ package ships (tuned_defaults.json) holds the batched defaults measured on
 GB300; the batched runner installs it for a matching GPU on first use.
 
   python -m paper_1409_0669_gb300.autotune --op copy --storage f32 --size 100000000
-  python -m paper_1409_0669_gb300.autotune --study --storage f32 --out tune.json
+  python -m paper_1409_0669_gb300.autotune --study [--paper-sizes] --storage f32 \
+      --out profiles/copy_first_study_f32_large.json
+  python -m paper_1409_0669_gb300.autotune --study-table profiles/copy_first_study_*.json
   python -m paper_1409_0669_gb300.autotune --buckets --op dot --storage f64 \
       --size 46416,215443,2154435,10000000 --out tune.json
   python -m paper_1409_0669_gb300.autotune --batch --op gemv_row --storage f32 \
@@ -210,25 +212,29 @@ def tune(op: str, storage: str, size, reps: int = 10, cfgs: Optional[List[LakCfg
 
 
 def copy_first_study(storage: str, sizes: Dict[str, object], keep_frac: float = 0.85,
-                     reps: int = 10) -> Dict:
+                     reps: int = 10, cfgs: Optional[List[LakCfg]] = None) -> Dict:
     """Sec. 3.2 / 3.4 on GB300: configurations within (1 - keep_frac) of the
-    best copy, evaluated on the other ops, against each op's own best."""
-    copy = tune("copy", storage, sizes["copy"], reps)
+    best copy, evaluated on the other ops, against each op's own best over the
+    same space (the whole space unless `cfgs` restricts it)."""
+    copy = tune("copy", storage, sizes["copy"], reps, cfgs)
     best = copy[0]["GBs"]
     cands = [r for r in copy if r["GBs"] >= keep_frac * best]
-    report = {"storage": storage, "copy_best_GBs": best, "candidates": len(cands),
-              "space": len(copy), "ops": {}}
+    report = {"storage": storage, "sizes": dict(sizes), "keep_frac": keep_frac,
+              "copy_best_GBs": best, "candidates": len(cands), "space": len(copy),
+              "candidate_cfgs": [r["cfg"] for r in cands], "ops": {}}
     cand_cfgs = [LakCfg(*r["cfg"]) for r in cands]
     per_op = {}
     for op in ("axpy", "dot", "gemv_row", "gemv_col", "spmv"):
-        own = tune(op, storage, sizes[op], reps)
         prob = Problem(op, storage, sizes[op])
+        own = tune(op, storage, sizes[op], reps, cfgs, prob)
         from_copy = tune(op, storage, sizes[op], reps, cand_cfgs, prob)
-        per_op[op] = {r_cfg: r for r_cfg, r in ((tuple(r["cfg"]), r) for r in from_copy)}
+        per_op[op] = {tuple(r["cfg"]): r for r in from_copy}
         report["ops"][op] = {
             "own_best": own[0], "best_from_copy": from_copy[0] if from_copy else None,
             "ratio": (from_copy[0]["GBs"] / own[0]["GBs"]) if from_copy and own else None,
             "default": _default_point(prob, reps)}
+        del prob
+        torch.cuda.empty_cache()
     # one shared configuration: the copy candidate with the best worst-case ratio
     shared, shared_score = None, -1.0
     for c in cands:
@@ -246,6 +252,39 @@ def copy_first_study(storage: str, sizes: Dict[str, object], keep_frac: float = 
     report["shared_worst_ratio"] = shared_score if shared else None
     report["copy_top"] = copy[:10]
     return report
+
+
+STUDY_SIZES = {
+    # the paper's own problem sizes (vectors of 2e6 entries, a 2048^2 matrix);
+    # the CSR product, which the paper leaves out, on the 64^3 Laplacian
+    "paper": {"copy": 2_000_000, "axpy": 2_000_000, "dot": 2_000_000,
+              "gemv_row": 2048, "gemv_col": 2048, "spmv": "lap3d_64"},
+    "large": {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
+              "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"},
+}
+
+_STUDY_OP_NAMES = {"axpy": "axpy", "dot": "dot", "gemv_row": "GEMV row", "gemv_col": "GEMV col",
+                   "spmv": "SpMV"}
+
+
+def study_table(reports: List[Dict]) -> str:
+    """Markdown table of copy-first study reports (one row per report and op):
+    each op's own best, the best copy-derived configuration, their ratio; then
+    one line per report with the shared configuration's worst-case ratio."""
+    lines = ["| storage, sizes | op | own best GB/s | best copy-derived GB/s | ratio |",
+             "|---|---|---|---|---|"]
+    notes = []
+    for rep in reports:
+        tag = f"{rep['storage'].upper()}, {rep.get('label', '?')}"
+        for op, name in _STUDY_OP_NAMES.items():
+            r = rep["ops"][op]
+            lines.append(f"| {tag} | {name} | {r['own_best']['GBs']:.0f} | "
+                         f"{r['best_from_copy']['GBs']:.0f} | {r['ratio']:.3f} |")
+        sc = rep["shared_cfg"]
+        notes.append(f"- {tag}: {rep['candidates']} of {rep['space']} configurations kept; "
+                     f"shared ({sc[0]}, {sc[1]}, {sc[2]}, {'local' if sc[3] else 'global'}) "
+                     f"reaches {100 * rep['shared_worst_ratio']:.1f} % of every op's own best")
+    return "\n".join(lines + [""] + notes) + "\n"
 
 
 # ---- batched launches -------------------------------------------------------------
@@ -439,6 +478,8 @@ def _main(argv=None):
     ap.add_argument("--study", action="store_true", help="copy-first transfer study")
     ap.add_argument("--paper-sizes", action="store_true",
                     help="run the study at the paper's sizes (2e6-entry vectors, 2048^2)")
+    ap.add_argument("--study-table", nargs="+", default=None, metavar="REPORT_JSON",
+                    help="print the markdown table of saved --study reports (no GPU needed)")
     ap.add_argument("--buckets", action="store_true",
                     help="one configuration per size bucket from the comma-separated --size list")
     ap.add_argument("--batch", action="store_true",
@@ -469,17 +510,16 @@ def _main(argv=None):
                            "cache": {f"{args.op}:{args.storage}:{b}": v["cfg"]
                                      for b, v in per.items()}}, indent=1)
     elif args.study:
-        if args.paper_sizes:
-            # the paper's own problem sizes (vectors of 2e6 entries, a 2048^2 matrix);
-            # the CSR product, which the paper leaves out, on the 64^3 Laplacian
-            sizes = {"copy": 2_000_000, "axpy": 2_000_000, "dot": 2_000_000,
-                     "gemv_row": 2048, "gemv_col": 2048, "spmv": "lap3d_64"}
-        else:
-            sizes = {"copy": 100_000_000, "axpy": 100_000_000, "dot": 100_000_000,
-                     "gemv_row": 16384, "gemv_col": 16384, "spmv": "lap3d_128"}
-        rep = copy_first_study(args.storage, sizes, reps=args.reps)
-        rep["sizes"] = sizes
+        label = "paper" if args.paper_sizes else "large"
+        rep = copy_first_study(args.storage, STUDY_SIZES[label], reps=args.reps)
+        rep["label"] = label
         text = json.dumps(rep, indent=1)
+    elif args.study_table:
+        reps_ = []
+        for path in args.study_table:
+            with open(path) as fh:
+                reps_.append(json.load(fh))
+        text = study_table(reps_)
     else:
         res = tune(args.op, args.storage, size, args.reps)
         text = json.dumps({"op": args.op, "storage": args.storage, "size": size,

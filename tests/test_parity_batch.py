@@ -32,9 +32,10 @@ def sizes(count, lo, hi, seed, extra=(0, 1, 2, 3)):
 def test_axpy_batch_vs_oracle(storage):
     """Every element of every instance against the oracle's y + alpha z rounded
     once to the storage type: bit-exact at alpha = 0.5 for FP32/FP64 (one
-    rounding on both sides), within one ulp at alpha = -1.25 and for BF16/FP16
-    (the kernel rounds its FP32 result once more).  Also identical bits to the
-    single-instance vec_axpy."""
+    rounding on both sides), within one ulp at alpha = -1.25 for FP32 (exact in
+    the oracle's FP64) and for BF16/FP16 (the kernel rounds its FP32 result
+    once more), within one FP64 rounding of each term for FP64 at -1.25.  Also
+    identical bits to the single-instance vec_axpy."""
     ns = sizes(300, 1, 200_000, 1)
     dt = synth.torch_dtype(storage)
     ys = [synth.uniform(n + 1, 10 + i, storage).cuda()[1:] if i % 7 == 0 else
@@ -46,10 +47,16 @@ def test_axpy_batch_vs_oracle(storage):
     b.run()
     torch.cuda.synchronize()
     for i, (x, y, z, a) in enumerate(zip(xs, ys, zs, alphas)):
-        ref = oracle.round_to(oracle.axpy(y.cpu(), z.cpu(), a), storage)
+        ref64 = oracle.axpy(y.cpu(), z.cpu(), a)
+        ref = oracle.round_to(ref64, storage)
         got = host(x)
         if a == 0.5 and storage in ("f32", "f64"):
             assert np.array_equal(got, ref), f"instance {i} (n={ns[i]}): alpha = 0.5 bit-exact"
+        elif storage == "f64":
+            # the oracle's own alpha * z is rounded in FP64 (the kernel fuses it):
+            # one rounding of each of |y + alpha z| and |alpha z| apart
+            bound = 2.0 ** -52 * (np.abs(ref64) + np.abs(a * host(z)))
+            assert np.all(np.abs(got - ref64) <= bound), f"instance {i} (n={ns[i]})"
         else:
             assert_ulp(got, ref, storage, 1.0, f"instance {i} (n={ns[i]})")
         single = torch.empty_like(x)
@@ -309,3 +316,36 @@ def test_batching_workload_sampled_instances_vs_oracle():
         ref = oracle.csr_spmv(rp.cpu(), ci.cpu(), v.cpu(), x.cpu())
         assert_normwise(host(y), ref, "f32", f"spmv instance {i} ({m} rows)")
     assert int(bs.workspace[:16].count_nonzero()) == 0
+
+
+def test_batches_take_the_shipped_tuned_defaults():
+    """A batch planned without a cfg on a GPU that the shipped autotuner cache
+    covers takes the cached launch shape (the built-in table is only the
+    fallback)."""
+    import json
+
+    from paper_1409_0669_gb300 import autotune
+    key = autotune.cache_key()
+    with open(B().TUNED_DEFAULTS) as fh:
+        entries = json.load(fh).get(key)
+    if not entries:
+        pytest.skip(f"no shipped batched defaults for {key}")
+    for name, cfg in entries.items():
+        _, op, storage = name.split(":")
+        dt = synth.torch_dtype(storage)
+        n = 1000
+        v = [torch.ones(n, dtype=dt, device="cuda")]
+        if op == "axpy":
+            b = B().axpy_batch(v, v, v, [0.5])
+        elif op == "dot":
+            b = B().dot_batch(v, v, [torch.zeros(1, dtype=torch.float64 if storage == "f64"
+                                                 else torch.float32, device="cuda")])
+        elif op == "gemv_row":
+            b = B().gemv_batch([torch.ones(4, n, dtype=dt, device="cuda")], v,
+                               [torch.zeros(4, dtype=dt, device="cuda")])
+        else:
+            rp, ci, vals = synth.laplacian_2d(8, storage)
+            b = B().spmv_batch([(rp.cuda(), ci.cuda(), vals.cuda(), 64)],
+                               [torch.ones(64, dtype=dt, device="cuda")],
+                               [torch.zeros(64, dtype=dt, device="cuda")])
+        assert tuple(b.info.cfg.as_tuple()) == tuple(cfg), (name, b.info.cfg.as_tuple(), cfg)
