@@ -117,22 +117,20 @@ __device__ __forceinline__ void seg_rows32(T *__restrict__ y, const int32_t *__r
             part = fma_acc(widen(val[j]), widen(ld_cached(x + col[j])), part);
         }
         // segmented scan of the open tails across lanes; lanes without entries
-        // end any carry, so they count as segment heads, and so does lane 0
+        // end any carry, so they count as segment heads, and so does lane 0.
+        // Each lane knows its distance to its segment's head from one ballot, so
+        // at step d it adds the value d lanes up only while d <= that distance
+        // (no head flag travels with the values: one shuffle per step)
         const bool starts_here = any && (nseg > 0 || !head_from_left);
         Ac incl = part;
-        bool flag = starts_here || !any;
+        const bool flag = starts_here || !any;
         const unsigned heads = __ballot_sync(0xffffffffu, flag) | 1u;
         const unsigned at_or_below = heads & (0xffffffffu >> (31 - lane));
         const int dist = lane - (31 - __clz((int)at_or_below));   // lanes back to the head
         const int span = __reduce_max_sync(0xffffffffu, dist);   // warp-uniform
-        // steps 1, 2, 4, ... up to span: the window 2^steps - 1 covers every run
         for (int d = 1; d <= span; d <<= 1) {
             const Ac v_up = __shfl_up_sync(0xffffffffu, incl, d);
-            const bool f_up = __shfl_up_sync(0xffffffffu, (int)flag, d) != 0;
-            if (lane >= d) {
-                if (!flag) incl += v_up;
-                flag = flag || f_up;
-            }
+            if (d <= dist) incl += v_up;
         }
         Ac carry = __shfl_up_sync(0xffffffffu, incl, 1);
         if (lane == 0 || !head_from_left) carry = Ac(0);

@@ -55,8 +55,9 @@ def test_gemv_rows_per_unit_and_spmv_units(nat):
     g = [nat.GemvDesc(256, 512, 768, m, n, max(n, 1))
          for m, n in ((2000, 64), (40, 4096), (3, 100000), (0, 5), (7, 0))]
     info, offs, _ = plan(nat, "gemv_row", "f32", g, cfg)
-    # rows per unit: 1024 -> 2 units; 16 -> 3 units; 1 -> 3 units; none; n = 0: all 7 -> 1
-    assert list(offs) == [0, 2, 5, 8, 8, 9]
+    # rows per unit: 1024 -> 2 units; 16 -> 3 units; 1, rounded up to the 2 rows a warp
+    # takes at once for long rows with 32-byte accesses -> 2 units; none; n = 0: all 7 -> 1
+    assert list(offs) == [0, 2, 5, 7, 7, 8]
     # CSR: one block's rows (64) per unit
     c = [nat.CsrDesc(256, 512, 768, 1024, 1280, m, m, 5 * m) for m in (1, 64, 65, 1000)]
     info, offs, _ = plan(nat, "spmv", "f32", c, nat.LakCfg(64, 0, 4, 0))
@@ -119,3 +120,26 @@ def test_batch_default_cfg_comes_from_the_installed_entry(nat, tmp_path, monkeyp
     finally:
         assert lib.lak_set_batch_default_cfg(nat.OPS["gemv_row"], nat.DTYPES["f32"], None) == 0
     assert plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple() == builtin
+
+
+def test_gemv_long_rows_period_and_units(nat):
+    """Long rows are taken R at a time by one warp, R rows a stride P apart that
+    start at the same offset modulo the access width: P is the smallest such
+    stride, and a unit holds a whole number of R * P rows."""
+    import struct
+    cases = [  # (n, lda, vec) -> (period, rows per warp)
+        (1001, 1001, 4, 4, 4),      # 4004 B rows, 16-byte accesses: P = 4, R = 4
+        (1002, 1002, 4, 2, 4),      # 4008 B: P = 2
+        (1024, 1024, 4, 1, 4),      # 4096 B: P = 1
+        (2049, 2049, 8, 8, 2),      # 32-byte accesses: P = 8, R = 2
+        (2050, 2052, 8, 2, 2),      # 8208 B rows: P = 2
+    ]
+    for n, lda, vec, P, R in cases:
+        m = 333
+        g = [nat.GemvDesc(256, 512, 768, m, n, lda)]
+        info, offs, raw = plan(nat, "gemv_row", "f32", g, nat.LakCfg(128, 0, vec, 0))
+        base = (64 + 8 * 2 + 15) // 16 * 16
+        rpu, vec_ok, group, period = struct.unpack_from("<qiii", raw, base + 48)
+        assert group == 32 and period == P, (n, lda, vec, group, period)
+        assert rpu % (R * P) == 0 and rpu >= 65536 // n
+        assert list(offs) == [0, -(-m // rpu)]
