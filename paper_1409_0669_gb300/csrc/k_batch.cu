@@ -51,14 +51,14 @@ struct GemvItem {
     int64_t rows_per_unit;
     int32_t vec_ok;
     int32_t group;           // lanes per row (power of two <= 32)
-    int32_t period;          // long rows: rows r and r + period share their alignment
+    int32_t period;          // groups of 8+ lanes: rows r and r + period share their alignment
     int32_t pad;
 };
 
-// Long rows (a whole warp per row) are taken R at a time by one warp: rows
+// Rows of lane groups of 8+ lanes are taken R at a time by one group: rows
 // r, r + P, ..., r + (R-1) P, which share their alignment to the access width,
 // so one x pack serves R rows and one reduction closes R sums.
-__host__ __device__ constexpr int gemv_rows_per_warp(int access_bytes) {
+__host__ __device__ constexpr int gemv_rows_per_group(int access_bytes) {
     return access_bytes <= 16 ? 4 : 2;
 }
 struct CsrItem {
@@ -227,65 +227,67 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // resident blocks keep twice the loads in flight, which pays for the few values
 // the cap spills to L1.
 //
-// Long rows (a whole warp per row) are taken R at a time (gemv_long_rows): one
-// x pack serves R rows, each lane keeps R loads of A in flight per x load, and
-// one reduction (halving exchanges, R + 4 shuffles) closes R sums instead of R
-// separate 5-shuffle reductions.  The R rows are r, r + P, ..., r + (R-1) P,
+// Rows of a lane group of 8 or more lanes (every row of 256+ FP32 entries at
+// 16-byte accesses) are taken R at a time per group (gemv_group_rows): one x
+// pack serves R rows, each lane keeps R loads of A in flight per x load, and one
+// reduction (halving exchanges, log2(G) + 1 shuffles for R = 4) closes R
+// sums instead of R separate ones.  The R rows are r, r + P, ..., r + (R-1) P,
 // with P the smallest row stride for which the rows start at the same offset
 // modulo the access width (P = 1 when lda * element size is a multiple of it),
 // so all R rows share one scalar head and one aligned body.  Measured on the
-// 4096-instance FP32 mix: 2.73 ms against 3.62 ms for one row per warp.
+// 4096-instance FP32 mix: 2.47 ms (6.05 TB/s) against 3.62 ms for one row per
+// lane group; FP64 7.8 against 9.0 ms, BF16 2.34 against 2.98 ms.
 
-// Sum of R per-lane values over the 32 lanes of a warp by halving exchanges:
-// afterwards lane l holds the total of value l >> (5 - log2 R), the same in
-// every lane of its group of 32 / R consecutive lanes.
+// Sum of R per-lane values over each aligned group of G lanes (G a power of two,
+// 8..32) by halving exchanges: afterwards lane lg of a group holds the total of
+// value lg / (G / R), the same in each of its G / R consecutive lanes.
 template <typename A, int R>
-__device__ __forceinline__ A warp_sum_rows(const A (&v)[R], int lane) {
+__device__ __forceinline__ A group_sum_rows(const A (&v)[R], int lg, int G) {
+    const int h1 = G >> 1;
+    const bool hi = lg & h1;
     if constexpr (R == 4) {
-        const bool hi = lane & 16;
-        const A r0 = __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[2], 16);
-        const A r1 = __shfl_xor_sync(0xffffffffu, hi ? v[1] : v[3], 16);
+        const int h2 = G >> 2;
+        const A r0 = __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[2], h1);
+        const A r1 = __shfl_xor_sync(0xffffffffu, hi ? v[1] : v[3], h1);
         const A k0 = (hi ? v[2] : v[0]) + r0;      // rows 0/2
         const A k1 = (hi ? v[3] : v[1]) + r1;      // rows 1/3
-        const bool h8 = lane & 8;
-        A k = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
-        k += __shfl_xor_sync(0xffffffffu, k, 4);
-        k += __shfl_xor_sync(0xffffffffu, k, 2);
-        k += __shfl_xor_sync(0xffffffffu, k, 1);
+        const bool h8 = lg & h2;
+        A k = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, h2);
+        for (int o = h2 >> 1; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
         return k;                                  // row (hi ? 2 : 0) + (h8 ? 1 : 0)
     } else {
-        const bool hi = lane & 16;
-        A k = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[1], 16);
-        k += __shfl_xor_sync(0xffffffffu, k, 8);
-        k += __shfl_xor_sync(0xffffffffu, k, 4);
-        k += __shfl_xor_sync(0xffffffffu, k, 2);
-        k += __shfl_xor_sync(0xffffffffu, k, 1);
+        A k = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[1], h1);
+        for (int o = h1 >> 1; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
         return k;                                  // row (hi ? 1 : 0)
     }
 }
 
 template <typename T, int V>
-__device__ __forceinline__ void gemv_long_rows(const GemvItem &it, int64_t r0, int64_t r1,
+__device__ __forceinline__ void gemv_group_rows(const GemvItem &it, int64_t r0, int64_t r1,
                                                int lane, int warp, int nwarps) {
     using Ac = typename Acc<T>::type;
     constexpr int ES = (int)sizeof(T);
     constexpr int W = V * ES > 32 ? 32 : V * ES;
-    constexpr int R = gemv_rows_per_warp(W);
+    constexpr int R = gemv_rows_per_group(W);
     const T *Am = static_cast<const T *>(it.d.A);
     const T *x = static_cast<const T *>(it.d.x);
     T *y = static_cast<T *>(it.d.y);
     const int64_t n = it.d.n, lda = it.d.lda;
+    const int G = it.group;                       // lanes per row group: 8, 16 or 32
+    const int ng = 32 / G;                        // row groups per warp
+    const int lg = lane % G, gi = lane / G;
     const int P = it.period;
     const int64_t span = (int64_t)R * P;
     const int64_t ngroups = (r1 - r0 + span - 1) / span * P;
-    for (int64_t g = warp; g < ngroups; g += nwarps) {          // warp-uniform
+    for (int64_t gb = (int64_t)warp * ng; gb < ngroups; gb += (int64_t)nwarps * ng) {  // warp-uniform
+        const int64_t g = gb + gi;
         const int64_t row0 = r0 + (g / P) * span + (g % P);
         const T *a[R];
         bool ok[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            ok[j] = row0 + (int64_t)j * P < r1;
-            a[j] = Am + (ok[j] ? row0 + (int64_t)j * P : row0) * lda;
+            ok[j] = g < ngroups && row0 + (int64_t)j * P < r1;
+            a[j] = Am + (ok[j] ? row0 + (int64_t)j * P : r0) * lda;
         }
         const int64_t mis = (int64_t)(((uintptr_t)a[0] % W) / ES);
         int64_t h = mis ? (int64_t)(W / ES) - mis : 0;
@@ -293,7 +295,7 @@ __device__ __forceinline__ void gemv_long_rows(const GemvItem &it, int64_t r0, i
         Ac acc[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[j] = Ac(0);
-        for (int64_t k = lane; k < h; k += 32) {
+        for (int64_t k = lg; k < h; k += G) {
             const Ac xv = widen(ld_cached(x + k));
 #pragma unroll
             for (int j = 0; j < R; ++j)
@@ -304,7 +306,7 @@ __device__ __forceinline__ void gemv_long_rows(const GemvItem &it, int64_t r0, i
         const T *xb = x + h;
         const bool xal = ((uintptr_t)xb % W) == 0;
 #pragma unroll 2
-        for (int64_t c = lane; c < nch; c += 32) {
+        for (int64_t c = lg; c < nch; c += G) {
             Pack<T, V> px;
             if (xal) {
                 load_pack<T, V, CACHED>(px, xb + c * V);
@@ -321,18 +323,18 @@ __device__ __forceinline__ void gemv_long_rows(const GemvItem &it, int64_t r0, i
                 for (int v = 0; v < V; ++v) acc[j] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[j]);
             }
         }
-        for (int64_t k = h + nch * V + lane; k < n; k += 32) {
+        for (int64_t k = h + nch * V + lg; k < n; k += G) {
             const Ac xv = widen(ld_cached(x + k));
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 if (ok[j]) acc[j] = fma_acc(widen(a[j][k]), xv, acc[j]);
         }
-        const Ac s = warp_sum_rows<Ac, R>(acc, lane);
-        constexpr int SH = R == 4 ? 3 : 4;                       // lanes per result: 2^SH
-        const int j = lane >> SH;
-        if ((lane & ((1 << SH) - 1)) == 0) {
+        const Ac s = group_sum_rows<Ac, R>(acc, lg, G);
+        const int per = G / R;                                  // lanes holding one row's sum
+        if (lg % per == 0) {
+            const int j = lg / per;
             const int64_t row = row0 + (int64_t)j * P;
-            if (row < r1) y[row] = narrow<T>(s);
+            if (g < ngroups && row < r1) y[row] = narrow<T>(s);
         }
     }
 }
@@ -358,8 +360,8 @@ gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
         const int lg = lane % G;
         const int64_t r0 = (u - __ldg(offs + i)) * it.rows_per_unit;
         const int64_t r1 = r0 + it.rows_per_unit < it.d.m ? r0 + it.rows_per_unit : it.d.m;
-        if (G == 32) {
-            gemv_long_rows<T, V>(it, r0, r1, lane, warp, nwarps);
+        if (G >= 8) {
+            gemv_group_rows<T, V>(it, r0, r1, lane, warp, nwarps);
             continue;
         }
         for (int64_t rb = r0 + (int64_t)warp * rpw; rb < r1; rb += (int64_t)nwarps * rpw) {
@@ -537,13 +539,13 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
         while (G < 32 && (int64_t)G * 2 * vec * 4 <= d.n) G *= 2;
         it.group = G;
         it.period = 1;
-        if (G == 32) {
+        if (G >= 8) {
             // rows r and r + P start at the same offset modulo the access width
             const int64_t rb = (d.lda * es) % w;
             int P = 1;
             while ((rb * P) % w) ++P;
             it.period = P;
-            const int64_t span = (int64_t)gemv_rows_per_warp(w) * P;
+            const int64_t span = (int64_t)gemv_rows_per_group(w) * P;
             it.rows_per_unit = (it.rows_per_unit + span - 1) / span * span;
         }
         return it;

@@ -123,23 +123,31 @@ def test_batch_default_cfg_comes_from_the_installed_entry(nat, tmp_path, monkeyp
 
 
 def test_gemv_long_rows_period_and_units(nat):
-    """Long rows are taken R at a time by one warp, R rows a stride P apart that
-    start at the same offset modulo the access width: P is the smallest such
-    stride, and a unit holds a whole number of R * P rows."""
+    """Rows of lane groups of 8+ lanes are taken R at a time by one group, R rows
+    a stride P apart that start at the same offset modulo the access width: P is
+    the smallest such stride, and a unit holds a whole number of R * P rows."""
     import struct
-    cases = [  # (n, lda, vec) -> (period, rows per warp)
-        (1001, 1001, 4, 4, 4),      # 4004 B rows, 16-byte accesses: P = 4, R = 4
-        (1002, 1002, 4, 2, 4),      # 4008 B: P = 2
-        (1024, 1024, 4, 1, 4),      # 4096 B: P = 1
-        (2049, 2049, 8, 8, 2),      # 32-byte accesses: P = 8, R = 2
-        (2050, 2052, 8, 2, 2),      # 8208 B rows: P = 2
+    cases = [  # (n, lda, vec) -> (lanes per row, period, rows per group)
+        (1001, 1001, 4, 32, 4, 4),      # 4004 B rows, 16-byte accesses: P = 4, R = 4
+        (1002, 1002, 4, 32, 2, 4),      # 4008 B: P = 2
+        (1024, 1024, 4, 32, 1, 4),      # 4096 B: P = 1
+        (300, 301, 4, 16, 4, 4),        # 16 lanes per row
+        (100, 101, 4, 8, 4, 4),         # 8 lanes per row
+        (2049, 2049, 8, 32, 8, 2),      # 32-byte accesses: P = 8, R = 2
+        (2050, 2052, 8, 32, 2, 2),      # 8208 B rows: P = 2
+        (300, 300, 8, 8, 2, 2),         # 8 lanes per row at 32 bytes: 1200 B rows, P = 2
     ]
-    for n, lda, vec, P, R in cases:
+    for n, lda, vec, G, P, R in cases:
         m = 333
         g = [nat.GemvDesc(256, 512, 768, m, n, lda)]
         info, offs, raw = plan(nat, "gemv_row", "f32", g, nat.LakCfg(128, 0, vec, 0))
         base = (64 + 8 * 2 + 15) // 16 * 16
         rpu, vec_ok, group, period = struct.unpack_from("<qiii", raw, base + 48)
-        assert group == 32 and period == P, (n, lda, vec, group, period)
-        assert rpu % (R * P) == 0 and rpu >= 65536 // n
+        assert group == G and period == P, (n, lda, vec, group, period)
+        assert rpu % (R * P) == 0 and rpu >= min(65536 // n, m)
         assert list(offs) == [0, -(-m // rpu)]
+    # 4 lanes per row (short rows at 32-byte accesses) keep one row per group
+    info, offs, raw = plan(nat, "gemv_row", "f32", [nat.GemvDesc(256, 512, 768, 50, 100, 101)],
+                           nat.LakCfg(128, 0, 8, 0))
+    rpu, _, group, period = struct.unpack_from("<qiii", raw, (64 + 16 + 15) // 16 * 16 + 48)
+    assert group == 4 and period == 1

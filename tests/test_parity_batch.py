@@ -84,8 +84,12 @@ def test_dot_batch_vs_oracle(storage):
     assert torch.all(b.workspace[:65536] == 0)
 
 
+@pytest.mark.parametrize("cfg", [None, (64, 0, 8, 0), (128, 0, 2, 0)], ids=str)
 @pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
-def test_gemv_batch_vs_oracle(storage):
+def test_gemv_batch_vs_oracle(storage, cfg):
+    """Instances of 1..700 rows and columns with padded leading dimensions:
+    rows go 1..4 at a time per lane group depending on the row length and the
+    access width (several rows a stride apart that share their alignment)."""
     ms = sizes(80, 1, 700, 3, extra=(1, 5, 0))
     ns = sizes(80, 1, 700, 4, extra=(1, 0, 9))
     dt = synth.torch_dtype(storage)
@@ -97,7 +101,7 @@ def test_gemv_batch_vs_oracle(storage):
         As.append(full[:, :n])
         xs.append(synth.uniform(n, 40 + i, storage).cuda())
         ys.append(torch.full((m,), float("nan"), dtype=dt, device="cuda"))
-    b = B().gemv_batch(As, xs, ys)
+    b = B().gemv_batch(As, xs, ys, cfg=cfg)
     b.run()
     torch.cuda.synchronize()
     for i, (A, x, y) in enumerate(zip(As, xs, ys)):
