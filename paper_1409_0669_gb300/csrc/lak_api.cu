@@ -172,8 +172,9 @@ DefaultCfg default_row(lak_op op, lak_dtype dt, int bucket) {
     return d;
 }
 
-// The batched persistent kernels (lak_batch_run) were tuned on their own, at
-// ~256 KB work units: they keep these launch shapes.
+// Fallback launch shapes of the batched persistent kernels (lak_batch_run), used
+// only where no autotuned entry is installed (lak_set_batch_default_cfg; the
+// package ships the entries it measured on GB300).
 struct BatchCfg {
     int block, bytes, inc;
 };
@@ -183,7 +184,7 @@ BatchCfg batch_row(lak_op op, lak_dtype dt) {
     switch (op) {
     case LAK_OP_AXPY: return {512, 64, LAK_INC_GLOBAL};
     case LAK_OP_DOT: return {512, f64 ? 32 : 16, LAK_INC_GLOBAL};
-    case LAK_OP_GEMV_ROW: return {64, 32, LAK_INC_GLOBAL};   // 3.62 vs 3.76 ms at 128
+    case LAK_OP_GEMV_ROW: return {128, 16, LAK_INC_GLOBAL};  // row groups take 4 rows each
     default: return {64, 16, LAK_INC_GLOBAL};      // CSR: 4 loads per lane (see batch_config)
     }
 }
