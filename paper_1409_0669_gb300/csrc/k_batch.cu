@@ -51,11 +51,11 @@ struct GemvItem {
     int64_t rows_per_unit;
     int32_t vec_ok;
     int32_t group;           // lanes per row (power of two <= 32)
-    int32_t period;          // groups of 8+ lanes: rows r and r + period share their alignment
+    int32_t period;          // groups of 4+ lanes: rows r and r + period share their alignment
     int32_t pad;
 };
 
-// Rows of lane groups of 8+ lanes are taken R at a time by one group: rows
+// Rows of lane groups of 4+ lanes are taken R at a time by one group: rows
 // r, r + P, ..., r + (R-1) P, which share their alignment to the access width,
 // so one x pack serves R rows and one reduction closes R sums.
 __host__ __device__ constexpr int gemv_rows_per_group(int access_bytes) {
@@ -227,8 +227,9 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // resident blocks keep twice the loads in flight, which pays for the few values
 // the cap spills to L1.
 //
-// Rows of a lane group of 8 or more lanes (every row of 256+ FP32 entries at
-// 16-byte accesses) are taken R at a time per group (gemv_group_rows): one x
+// Rows of a lane group of 4 or more lanes (every row when a lane reads at most
+// 32 bytes per access, as a group reads at least 128 bytes of a row per step)
+// are taken R at a time per group (gemv_group_rows): one x
 // pack serves R rows, each lane keeps R loads of A in flight per x load, and one
 // reduction (halving exchanges, log2(G) + 1 shuffles for R = 4) closes R
 // sums instead of R separate ones.  The R rows are r, r + P, ..., r + (R-1) P,
@@ -239,7 +240,7 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // lane group; FP64 7.8 against 9.0 ms, BF16 2.34 against 2.98 ms.
 
 // Sum of R per-lane values over each aligned group of G lanes (G a power of two,
-// 8..32) by halving exchanges: afterwards lane lg of a group holds the total of
+// 4..32) by halving exchanges: afterwards lane lg of a group holds the total of
 // value lg / (G / R), the same in each of its G / R consecutive lanes.
 template <typename A, int R>
 __device__ __forceinline__ A group_sum_rows(const A (&v)[R], int lg, int G) {
@@ -273,7 +274,7 @@ __device__ __forceinline__ void gemv_group_rows(const GemvItem &it, int64_t r0, 
     const T *x = static_cast<const T *>(it.d.x);
     T *y = static_cast<T *>(it.d.y);
     const int64_t n = it.d.n, lda = it.d.lda;
-    const int G = it.group;                       // lanes per row group: 8, 16 or 32
+    const int G = it.group;                       // lanes per row group: 4 .. 32
     const int ng = 32 / G;                        // row groups per warp
     const int lg = lane % G, gi = lane / G;
     const int P = it.period;
@@ -360,7 +361,7 @@ gemv_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict_
         const int lg = lane % G;
         const int64_t r0 = (u - __ldg(offs + i)) * it.rows_per_unit;
         const int64_t r1 = r0 + it.rows_per_unit < it.d.m ? r0 + it.rows_per_unit : it.d.m;
-        if (G >= 8) {
+        if (G >= 4) {
             gemv_group_rows<T, V>(it, r0, r1, lane, warp, nwarps);
             continue;
         }
@@ -539,7 +540,7 @@ LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_d
         while (G < 32 && (int64_t)G * 2 * vec * 4 <= d.n) G *= 2;
         it.group = G;
         it.period = 1;
-        if (G >= 8) {
+        if (G >= 4) {
             // rows r and r + P start at the same offset modulo the access width
             const int64_t rb = (d.lda * es) % w;
             int P = 1;

@@ -146,8 +146,14 @@ def test_gemv_long_rows_period_and_units(nat):
         assert group == G and period == P, (n, lda, vec, group, period)
         assert rpu % (R * P) == 0 and rpu >= min(65536 // n, m)
         assert list(offs) == [0, -(-m // rpu)]
-    # 4 lanes per row (short rows at 32-byte accesses) keep one row per group
+    # 4 lanes per row (short rows at 32-byte accesses) take 2 rows at a time too
     info, offs, raw = plan(nat, "gemv_row", "f32", [nat.GemvDesc(256, 512, 768, 50, 100, 101)],
                            nat.LakCfg(128, 0, 8, 0))
     rpu, _, group, period = struct.unpack_from("<qiii", raw, (64 + 16 + 15) // 16 * 16 + 48)
-    assert group == 4 and period == 1
+    assert group == 4 and period == 8 and rpu % 16 == 0
+    # FP64 at 16 elements per access (two 32-byte loads): 1-2 lanes per short row,
+    # one row at a time
+    info, offs, raw = plan(nat, "gemv_row", "f64", [nat.GemvDesc(256, 512, 768, 50, 100, 101)],
+                           nat.LakCfg(128, 0, 16, 0))
+    rpu, _, group, period = struct.unpack_from("<qiii", raw, (64 + 16 + 15) // 16 * 16 + 48)
+    assert group < 4 and period == 1

@@ -216,3 +216,43 @@ def test_headline_is_compact_and_complete():
                 "size_curves"):
         assert big not in line
     assert json.loads(text)["value"] == round(5266.123456789, 2)
+
+
+def test_cpu_chunks_cover_the_sample_exactly():
+    """The all-cores CPU leg runs the oracle on fixed chunks of the sample: the
+    chunks' bytes add up to the sample's, and the chunked results are the
+    single-call results (GEMV and CSR rows concatenate to the full product; the
+    chunked dot's hi + lo parts add up to the full dot)."""
+    sys.path.insert(0, ROOT)
+    import math
+
+    import numpy as np
+
+    import bench
+    import oracle
+    items = bench.cpu_sample_items()
+    chunks = bench.cpu_chunks(items)
+    assert abs(sum(b for _, b in chunks) - sum(it[2] for it in items)) < 1e-6 * sum(
+        it[2] for it in items)
+    pos = 0
+    for _, _, b, call in items:
+        kind = call[0]
+        got, acc = [], 0.0
+        while acc < b * (1 - 1e-12):
+            fn, cb = chunks[pos]
+            got.append(fn())
+            acc += cb
+            pos += 1
+        if kind == "dot":
+            parts = [p for hi_lo in got for p in hi_lo]
+            assert math.isclose(math.fsum(parts), oracle.dot(call[1], call[2]), rel_tol=1e-15,
+                                abs_tol=1e-300)
+        elif kind == "gemv":
+            _, A, x, g, lay = call
+            assert np.array_equal(np.concatenate(got), oracle.gemv(A, x, g, g, g, lay))
+        elif kind == "spmv":
+            assert np.array_equal(np.concatenate(got),
+                                  oracle.csr_spmv(call[1], call[2], call[3], call[4]))
+        elif kind == "axpy":
+            assert np.array_equal(np.concatenate(got), oracle.axpy(call[1], call[2], 0.5))
+    assert pos == len(chunks)
