@@ -98,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -108,9 +108,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
+        """Summary of the samples; with window = (t0, t1) (time.monotonic()
+        values around the timed region) only the samples taken inside it, if
+        any arrived there."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -122,7 +125,12 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        lines = [ln for _, ln in self.lines]
+        if window is not None:
+            inside = [ln for t, ln in self.lines if window[0] <= t <= window[1]]
+            if inside:
+                lines = inside
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -1465,15 +1473,17 @@ def run_gb300(args):
     time.sleep(0.3)
     barrier(dist, device)
     torch.cuda.synchronize()
+    t_window = time.monotonic()
     with torch.cuda.stream(stream):
         start.record()
         for k in range(K):
             run_step(items, lib_check, ev[k])
         stop.record()
     torch.cuda.synchronize()
+    t_window = (t_window, time.monotonic())
     barrier(dist, device)
     time.sleep(0.2)
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_window)
     elapsed_ms = start.elapsed_time(stop)
     elapsed_ms = max_over_ranks(elapsed_ms, dist, device)
 

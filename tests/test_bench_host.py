@@ -256,3 +256,29 @@ def test_cpu_chunks_cover_the_sample_exactly():
         elif kind == "axpy":
             assert np.array_equal(np.concatenate(got), oracle.axpy(call[1], call[2], 0.5))
     assert pos == len(chunks)
+
+
+def test_clock_samples_are_taken_from_the_timed_window():
+    """Only nvidia-smi samples that arrived while the timed region ran count
+    (when any did); throttle reasons are read from the same samples."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc = _Proc()
+    row = "{mhz}, 2070, 500.0, 0x0, {hw}, Not Active, Not Active, Not Active"
+    s.lines = [(1.0, row.format(mhz=1000, hw="Active")),        # before: idle, throttled
+               (2.0, row.format(mhz=2070, hw="Not Active")),
+               (2.5, row.format(mhz=2060, hw="Not Active")),
+               (9.0, row.format(mhz=900, hw="Not Active"))]     # after
+    c = s.stop((1.5, 3.0))
+    assert c["samples"] == 2 and c["sm_mhz"] == 2065.0 and c["reasons"] == []
+    c = s.stop((5.0, 6.0))                 # nothing inside: every sample counts
+    assert c["samples"] == 4 and c["reasons"] == ["hw_slowdown"]
