@@ -353,3 +353,41 @@ def test_batches_take_the_shipped_tuned_defaults():
                                [torch.ones(64, dtype=dt, device="cuda")],
                                [torch.zeros(64, dtype=dt, device="cuda")])
         assert tuple(b.info.cfg.as_tuple()) == tuple(cfg), (name, b.info.cfg.as_tuple(), cfg)
+
+
+@pytest.mark.parametrize("vec", [2, 4, 8, 16])
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16"])
+def test_gemv_batch_adversarial_shapes(storage, vec):
+    """Row counts below and around the rows a lane group takes at once, row
+    lengths around the access width and the lane-group thresholds, leading
+    dimensions that give every alignment period, and matrices starting 0..3
+    elements past an aligned address: every instance against the oracle."""
+    dt = synth.torch_dtype(storage)
+    ms = (1, 2, 3, 4, 5, 7, 8, 9, 17, 33)
+    ns = (1, 2, 3, 5, 8, 9, 31, 33, 64, 65, 129, 257, 513, 1025)
+    shapes = [(m, n, pad, off) for i, (m, n) in enumerate((m, n) for m in ms for n in ns)
+              for pad, off in [((i * 7) % 4, (i * 5) % 4)]]
+    total = sum(off + m * (n + pad) for m, n, pad, off in shapes) + 64
+    flat = synth.normal((total,), 600, storage).cuda()
+    As, xs, ys, metas = [], [], [], []
+    o = 0
+    for i, (m, n, pad, off) in enumerate(shapes):
+        o += off
+        A = flat[o:o + m * (n + pad)].view(m, n + pad)[:, :n]
+        o += m * (n + pad)
+        As.append(A)
+        xs.append(synth.uniform(n, 700 + i, storage).cuda())
+        ys.append(torch.full((m,), float("nan"), dtype=dt, device="cuda"))
+        metas.append((m, n, n + pad))
+    b = B().gemv_batch(As, xs, ys, cfg=(128, 0, vec, 0))
+    b.run()
+    torch.cuda.synchronize()
+    for i, (A, x, y, (m, n, lda)) in enumerate(zip(As, xs, ys, metas)):
+        sub = A.contiguous().reshape(-1).cpu()              # the instance's own entries
+        ref = oracle.gemv(sub, x.cpu(), m, n, n, "row")
+        abs_ref = oracle.gemv(np.abs(oracle.widen(sub)), np.abs(host(x)), m, n, n, "row")
+        what = f"instance {i} {m}x{n} lda {lda} vec {vec}"
+        if storage == "bf16":
+            assert_reduced_sum(host(y), ref, abs_ref, np.full(m, n), storage, what)
+        else:
+            assert_normwise_scaled(host(y), ref, abs_ref, storage, what)
