@@ -177,11 +177,22 @@ def set_default_cfg(op: str, storage: str, cfg: CfgLike, bucket: Optional[int] =
     _dot_ws_sizes.clear()                 # workspace needs follow the defaults
 
 
-def set_batch_default_cfg(op: str, storage: str, cfg: CfgLike):
-    """Replace (or with cfg=None restore) the launch configuration that
-    batched launches of `op` take when planned without one."""
+# (op, storage) pairs whose batched default the caller set: the shipped
+# autotuned defaults, installed when the first batch is planned, leave them alone
+_user_batch_defaults = set()
+
+
+def _apply_batch_default(op: str, storage: str, cfg: CfgLike):
     _native.check("lak_set_batch_default_cfg",
                   _lib.lak_set_batch_default_cfg(OPS[op], DTYPES[storage], _cfg_ptr(cfg)))
+
+
+def set_batch_default_cfg(op: str, storage: str, cfg: CfgLike):
+    """Replace (or with cfg=None restore the built-in shape of) the launch
+    configuration that batched launches of `op` take when planned without one.
+    Process-wide; takes precedence over the shipped autotuned defaults."""
+    _apply_batch_default(op, storage, cfg)
+    _user_batch_defaults.add((op, storage))
 
 
 def probe_fma_f64(iters: int, grid: Optional[int] = None, block: int = 256,

@@ -497,11 +497,11 @@ def _main(argv=None):
         res = tune_batch(args.op, args.storage, args.count, reps=min(args.reps, 5))
         # the built-in shape: time a plan without a cfg with any installed entry
         # removed (the batched runner installs the shipped cache on first use)
+        from . import _apply_batch_default
         from . import batch as _B
-        from . import set_batch_default_cfg
         prob_default = BatchProblem(args.op, args.storage, args.count)
         _B.install_tuned_defaults()
-        set_batch_default_cfg(args.op, args.storage, None)
+        _apply_batch_default(args.op, args.storage, None)
         default_us = prob_default.time_cfg(None)
         del prob_default
         _B._installed.discard(torch.cuda.current_device())

@@ -35,16 +35,30 @@ _installed = set()
 def install_tuned_defaults(path: str = TUNED_DEFAULTS) -> int:
     """Install the batched launch defaults the autotuner measured for this GPU
     model (its "batch:<op>:<storage>" entries; other GPUs keep the built-in
-    shapes).  Runs once per device per process, on the first batch planned
-    there; returns the number of entries installed."""
+    shapes), except where the caller has set a default itself
+    (set_batch_default_cfg).  Runs once per device per process, on the first
+    batch planned there; returns the number of entries installed.  The
+    defaults are process-wide."""
     dev = torch.cuda.current_device()
     if dev in _installed:
         return 0
     _installed.add(dev)
     if not os.path.exists(path):
         return 0
-    from .autotune import apply_cache
-    return apply_cache(path, only_batch=True)
+    import json
+
+    from . import _apply_batch_default, _user_batch_defaults
+    from .autotune import cache_key
+    with open(path) as fh:
+        entries = json.load(fh).get(cache_key(), {})
+    done = 0
+    for key, cfg in entries.items():
+        parts = key.split(":")
+        if parts[0] != "batch" or (parts[1], parts[2]) in _user_batch_defaults:
+            continue
+        _apply_batch_default(parts[1], parts[2], tuple(cfg))
+        done += 1
+    return done
 
 
 def _cfg(cfg):

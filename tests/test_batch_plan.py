@@ -110,8 +110,11 @@ def test_batch_default_cfg_comes_from_the_installed_entry(nat, tmp_path, monkeyp
         assert lib.lak_set_batch_default_cfg(nat.OPS["copy"], 0, None) == nat.LAK_EINVAL
         # the autotuner's cache file format, installed through apply_cache
         import json
+
+        import paper_1409_0669_gb300 as lak
         from paper_1409_0669_gb300 import autotune
         monkeypatch.setattr(autotune, "cache_key", lambda: "TEST GPU|sms=152")
+        monkeypatch.setattr(lak, "_user_batch_defaults", set())     # leave no trace
         path = tmp_path / "cache.json"
         path.write_text(json.dumps({"TEST GPU|sms=152": {"batch:gemv_row:f32": [32, 0, 8, 0]},
                                     "OTHER|sms=1": {"batch:gemv_row:f32": [128, 0, 2, 0]}}))
@@ -157,3 +160,32 @@ def test_gemv_long_rows_period_and_units(nat):
                            nat.LakCfg(128, 0, 16, 0))
     rpu, _, group, period = struct.unpack_from("<qiii", raw, (64 + 16 + 15) // 16 * 16 + 48)
     assert group < 4 and period == 1
+
+
+def test_shipped_defaults_leave_caller_settings_alone(nat, tmp_path, monkeypatch):
+    """The batched runner installs the shipped autotuned defaults when the first
+    batch is planned, but not over a default the caller set before."""
+    import json
+
+    import paper_1409_0669_gb300 as lak
+    from paper_1409_0669_gb300 import autotune
+    from paper_1409_0669_gb300 import batch as B
+    lib = nat.load()
+    monkeypatch.setattr(autotune, "cache_key", lambda: "TEST GPU|sms=152")
+    monkeypatch.setattr(B.torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(B, "_installed", set())
+    monkeypatch.setattr(lak, "_user_batch_defaults", set())
+    path = tmp_path / "shipped.json"
+    path.write_text(json.dumps({"TEST GPU|sms=152": {"batch:gemv_row:f32": [32, 0, 8, 0],
+                                                     "batch:axpy:f32": [256, 0, 4, 0]}}))
+    g = [nat.GemvDesc(256, 512, 768, 100, 1000, 1000)]
+    a = [nat.AxpyDesc(256, 512, 768, 1000, 0.5)]
+    try:
+        lak.set_batch_default_cfg("gemv_row", "f32", (64, 0, 4, 0))     # the caller's
+        assert B.install_tuned_defaults(str(path)) == 1                 # axpy only
+        assert plan(nat, "gemv_row", "f32", g)[0].cfg.as_tuple() == (64, 0, 4, 0)
+        assert plan(nat, "axpy", "f32", a)[0].cfg.as_tuple() == (256, 0, 4, 0)
+        assert B.install_tuned_defaults(str(path)) == 0                 # once per device
+    finally:
+        for op in ("gemv_row", "axpy"):
+            assert lib.lak_set_batch_default_cfg(nat.OPS[op], nat.DTYPES["f32"], None) == 0
