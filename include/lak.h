@@ -108,10 +108,12 @@ typedef struct {
     int32_t increment;
 } lak_cfg;
 
-/* Message for the calling thread's most recent failed call ("" if none). */
+/* Message for the calling thread's most recent failed call ("" if none).
+ * Library infrastructure: no counterpart in the paper. */
 LAK_API const char *lak_last_error(void);
 
-/* ABI version of this header (bumped on any incompatible change). */
+/* ABI version of this header (bumped on any incompatible change).  Library
+ * infrastructure: no counterpart in the paper. */
 LAK_API int32_t lak_abi_version(void);
 
 /*
@@ -129,7 +131,9 @@ LAK_API int32_t lak_abi_version(void);
 
 /*
  * The size bucket (0 .. LAK_SIZE_BUCKETS-1) a call of `op` with these sizes
- * falls in (sizes as in lak_resolve_cfg), or a negative lak_status.
+ * falls in (sizes as in lak_resolve_cfg), or a negative lak_status.  The
+ * buckets refine the paper's one configuration per device and operation
+ * (Sec. 3).
  */
 LAK_API int32_t lak_size_bucket(lak_op op, lak_dtype dtype, int64_t m, int64_t n, int64_t nnz);
 
@@ -137,16 +141,19 @@ LAK_API int32_t lak_size_bucket(lak_op op, lak_dtype dtype, int64_t m, int64_t n
  * Replace the default configuration used for (op, dtype) in size bucket
  * `bucket` (-1: every bucket) when a call passes no explicit cfg; cfg = NULL
  * restores the built-in default.  Process-wide; not synchronised against
- * concurrent calls that read it.
+ * concurrent calls that read it.  (Sec. 3.4: the configuration chosen for a
+ * device, here per size bucket.)
  */
 LAK_API lak_status lak_set_default_cfg_bucket(lak_op op, lak_dtype dtype, int32_t bucket,
                                               const lak_cfg *cfg);
 
-/* lak_set_default_cfg_bucket(op, dtype, -1, cfg): every size bucket. */
+/* lak_set_default_cfg_bucket(op, dtype, -1, cfg): every size bucket (the
+ * paper's single configuration per device and operation, Sec. 3.4). */
 LAK_API lak_status lak_set_default_cfg(lak_op op, lak_dtype dtype, const lak_cfg *cfg);
 
 /*
- * The configuration a call of `op` would launch with on the current device,
+ * The configuration (Sec. 1: local and global work size, with Sec. 2's vector
+ * length and increment) a call of `op` would launch with on the current device,
  * after defaults and automatic fields are filled in.  Sizes: for the vector
  * ops m = n = the vector length; for dense_gemv the matrix is m-by-n; for
  * csr_spmv m rows, n columns and nnz stored entries (nnz is ignored by the
@@ -199,8 +206,8 @@ LAK_API lak_status vec_axpby_strided(void *x, int64_t incx, double alpha, const 
 
 /*
  * vec_axpy_norm2: x[i] = y[i] + alpha * z[i] and *out = sum_i x[i]^2 of the
- * stored x, in one pass (the update fused with the inner product of its result
- * with itself: 3n elements moved instead of 5n for vec_axpy then vec_dot).
+ * stored x, in one pass (Sec. 2's vector update fused with Sec. 2's inner
+ * product of its result with itself: 3n elements moved instead of 5n for vec_axpy then vec_dot).
  * Reduction, `out` type and workspace rules as for vec_dot; the workspace size
  * comes from vec_axpy_norm2_workspace.
  */
@@ -210,8 +217,9 @@ LAK_API lak_status vec_axpy_norm2(void *x, const void *y, const void *z, double 
                                   const lak_cfg *cfg, void *stream);
 
 /*
- * Workspace bytes vec_dot needs for these arguments on the current device
- * (a partial sum per block and one arrival counter).  0 on invalid input.
+ * Workspace bytes vec_dot (Sec. 2's inner product) needs for these arguments on
+ * the current device (a partial sum per block and one arrival counter).  0 on
+ * invalid input.
  */
 LAK_API size_t vec_dot_workspace(int64_t n, lak_dtype dtype, const lak_cfg *cfg);
 
@@ -319,8 +327,9 @@ LAK_API lak_status vec_dot_noalloc(void *out, const void *x, const void *y, int6
                                    lak_dtype dtype, const lak_cfg *cfg, void *stream);
 
 /*
- * Workspace bytes dense_gemv needs (column-major split-K partials and per-tile
- * counters; 0 for row-major) on the current device.
+ * Workspace bytes dense_gemv (Sec. 2's matrix-vector product) needs
+ * (column-major split-K partials and per-tile counters; 0 for row-major) on the
+ * current device.
  */
 LAK_API size_t dense_gemv_workspace(int64_t m, int64_t n, lak_layout layout,
                                     lak_dtype dtype, const lak_cfg *cfg);
@@ -348,8 +357,8 @@ LAK_API lak_status dense_gemv(void *y, const void *A, const void *x, int64_t m,
 
 /*
  * dense_gemv_axpby: y = alpha * A x + beta * y, same layouts, workspace and
- * configuration as dense_gemv (the GEMV and the vector update fused: y is read
- * only when beta != 0).  dense_gemv is the alpha = 1, beta = 0 case.
+ * configuration as dense_gemv (Sec. 2's matrix-vector product and vector update
+ * fused: y is read only when beta != 0).  dense_gemv is the alpha = 1, beta = 0 case.
  */
 LAK_API lak_status dense_gemv_axpby(void *y, double alpha, const void *A, const void *x,
                                     double beta, int64_t m, int64_t n, int64_t lda,
@@ -358,8 +367,8 @@ LAK_API lak_status dense_gemv_axpby(void *y, double alpha, const void *A, const 
 
 /*
  * dense_gemv_trans: y = A^T x for the m-by-n matrix A stored as for dense_gemv
- * (y has n elements, x has m): the product in the other layout of the same
- * storage.  Workspace: dense_gemv_workspace(n, m, <the other layout>, ...).
+ * (y has n elements, x has m): Sec. 2's matrix-vector product in the other
+ * layout of the same storage.  Workspace: dense_gemv_workspace(n, m, <the other layout>, ...).
  */
 LAK_API lak_status dense_gemv_trans(void *y, const void *A, const void *x, int64_t m, int64_t n,
                                     int64_t lda, lak_layout layout, lak_dtype dtype,
@@ -422,7 +431,8 @@ LAK_API lak_status csr_to_sell_fill(const int32_t *row_ptr, const int32_t *col_i
                                     void *stream);
 LAK_API lak_status sell_pack_values(void *sell_vals, const void *csr_vals, const int32_t *map,
                                     int64_t total, lak_dtype dtype, void *stream);
-/* y[perm[p]] = sum over the row at position p, for the m rows.  cfg: block
+/* The SELL-C-sigma product (outside the paper, Sec. 1, like every sparse
+ * format): y[perm[p]] = sum over the row at position p, for the m rows.  cfg: block
  * (warps of it each take a slice), grid (0 = one warp per slice), vec (slots
  * loaded per lane per step), increment; NULL = (256, 0, 4, global). */
 LAK_API lak_status sell_spmv(void *y, const int64_t *slice_ptr, const int32_t *slice_len,
@@ -441,21 +451,24 @@ LAK_API lak_status sell_spmv(void *y, const int64_t *slice_ptr, const int32_t *s
  * ---------------------------------------------------------------------- */
 
 /* dA[i*ldd + j] = dy[i] * x[j] for i < m, j < n (ldd >= n); one product
- * rounded once to the storage type. */
+ * rounded once to the storage type.  Derivative building block: no counterpart
+ * in the paper. */
 LAK_API lak_status dense_outer(void *dA, const void *dy, const void *x, int64_t m, int64_t n,
                                int64_t ldd, lak_dtype dtype, void *stream);
 
 /* dvals[k] = dy[i] * x[col_idx[k]] for every stored entry k of row i of an
  * m-row CSR pattern with nnz entries (the gradient of the CSR product with
- * respect to its values). */
+ * respect to its values; no counterpart in the paper). */
 LAK_API lak_status csr_sampled_outer(void *dvals, const int32_t *row_ptr, const int32_t *col_idx,
                                      const void *dy, const void *x, int64_t m, int64_t nnz,
                                      lak_dtype dtype, void *stream);
 
-/* Workspace bytes csr_transpose needs for a matrix with n columns. */
+/* Workspace bytes csr_transpose needs for a matrix with n columns (derivative
+ * building block; no counterpart in the paper). */
 LAK_API size_t csr_transpose_workspace(int64_t n);
 
-/* The CSC form of an m-by-n CSR pattern: col_ptr (n+1), row_idx (nnz) and
+/* The CSC form of an m-by-n CSR pattern (derivative building block; no
+ * counterpart in the paper): col_ptr (n+1), row_idx (nnz) and
  * perm (nnz), perm[q] = the CSR position of the q-th CSC entry, entries of
  * each column in increasing CSR position (the result of a stable counting
  * sort; deterministic).  (col_ptr, row_idx) with values vals[perm] is A^T in
@@ -466,12 +479,14 @@ LAK_API lak_status csr_transpose(int32_t *col_ptr, int32_t *row_idx, int32_t *pe
                                  int64_t n, int64_t nnz, void *workspace, size_t ws_bytes,
                                  void *stream);
 
-/* dst[i] = src[idx[i]] for i < n (a bit copy of elements of `dtype`). */
+/* dst[i] = src[idx[i]] for i < n (a bit copy of elements of `dtype`; derivative
+ * building block, no counterpart in the paper). */
 LAK_API lak_status vec_gather(void *dst, const void *src, const int32_t *idx, int64_t n,
                               lak_dtype dtype, void *stream);
 
 /* out[i] = alpha * v[i], alpha ONE DEVICE element: float for F32/BF16/F16,
- * double for F64 (the type vec_dot writes). */
+ * double for F64 (the type vec_dot writes).  Derivative building block (the
+ * inner product's gradient); no counterpart in the paper. */
 LAK_API lak_status vec_scale_dev(void *out, const void *v, const void *alpha, int64_t n,
                                  lak_dtype dtype, void *stream);
 
@@ -528,6 +543,8 @@ typedef struct {
     int32_t dtype;
 } lak_batch_info;
 
+/* Plan a batch on the host, then run it (see above; no counterpart in the
+ * paper, which runs one operation at a time). */
 LAK_API lak_status lak_batch_plan(lak_op op, lak_dtype dtype, const void *host_descs, int64_t count,
                                   const lak_cfg *cfg, void *host_table, size_t table_bytes,
                                   lak_batch_info *info);

@@ -193,3 +193,17 @@ def test_binding_refuses_operands_on_another_device(lib, monkeypatch):
     from paper_1409_0669_gb300 import batch
     with pytest.raises(ValueError, match="cuda:1"):
         batch._ptr(_FakeCudaTensor(1))
+
+
+def test_every_entry_point_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each declaration's own comment (the nearest one before it) cites the
+    paper's section that defines the operation, or states that the paper has
+    no counterpart."""
+    text = open(HEADER).read()
+    missing = []
+    for m in re.finditer(r"LAK_API\s+[\w\s\*]+?\b(\w+)\s*\(", text):
+        before = text[:m.start()]
+        comment = before[before.rfind("/*"):]
+        if not re.search(r"Sec\.|counterpart", comment):
+            missing.append(m.group(1))
+    assert not missing, missing
