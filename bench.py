@@ -1356,7 +1356,7 @@ def _r(v, nd):
 
 
 def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_step, launches,
-             roofline, per_kernel, e2e, cpu, clocks, detail_path, probe=None):
+             roofline, per_kernel, e2e, cpu, clocks, detail_path, probe=None, gprobe=None):
     """The one JSON line the run ends with: the headline metric and the keys a
     reader needs to check it (roofline of the dominant kernel, per-kernel
     GB/s at the largest sizes, end to end, CPU baseline, clocks), kept within
@@ -1427,6 +1427,9 @@ def headline(*, value, ms_per_step, steps, warmup, world, workload, bytes_per_st
     if probe is not None:
         line["fp64_probe"] = {"tflops": _r(probe.get("tflops"), 4), "sm_mhz": probe.get("sm_mhz"),
                               "fma_per_sm_per_clk": _r(probe.get("fma_per_sm_per_clk"), 3)}
+    if gprobe is not None:
+        line["gather_probe"] = {"G_per_s": _r(gprobe.get("gathers_per_s", 0) / 1e9, 1),
+                                "per_sm_per_clk": _r(gprobe.get("per_sm_per_clk"), 3)}
     if detail_path:
         line["detail"] = os.path.basename(detail_path)
     return line
@@ -1555,6 +1558,7 @@ def run_gb300(args):
     # the matrix's own entries (vec_dot_sparse) timed alone
     with torch.cuda.stream(stream):
         floors = gather_floors(per, lak)
+        gprobe = gather_probe(device)
     # The sparse inner product is a floor only where the columns are random (the
     # power-law matrix): a stencil's x reuse lets a row-parallel kernel beat an
     # entry-parallel gather, so there it is reported but the roof stays HBM.
@@ -1629,7 +1633,7 @@ def run_gb300(args):
 
     workload = WORKLOAD if not args.only else f"subset /{args.only}/ of: " + WORKLOAD
     detail = {"per_kernel": summary, "roofline": roofline, "e2e": e2e, "clocks": clocks,
-              "fp64_probe": probe,
+              "fp64_probe": probe, "gather_probe": gprobe,
               "config": {"workload": workload, "bytes_per_step": bytes_per_step,
                          "launches_per_step": len(items)}}
     for key, val in (("cpu_baseline", cpu), ("precision", precision), ("batched", batched),
@@ -1645,7 +1649,8 @@ def run_gb300(args):
     line = headline(value=value, ms_per_step=ms_per_step, steps=K, warmup=W, world=world,
                     workload=workload, bytes_per_step=bytes_per_step,
                     launches=len(items), roofline=roofline, per_kernel=summary, e2e=e2e,
-                    cpu=cpu, clocks=clocks, detail_path=detail_path, probe=probe)
+                    cpu=cpu, clocks=clocks, detail_path=detail_path, probe=probe,
+                    gprobe=gprobe)
     if rank == 0:
         print(json.dumps(line, separators=(",", ":")))
     if dist is not None:
@@ -1723,6 +1728,37 @@ def gather_floors(per, lak, reps=20):
         out[f"spmv_{name.split('_')[1]}_{it.dtype}"] = (us, name)
         del ws
     return out
+
+
+def gather_probe(device, n_gather=32_000_000, n_y=2_000_000, reps=20):
+    """The rate of fully random 4-byte gathers: vec_dot_sparse over n_gather
+    uniformly random indices into an FP32 vector of n_y entries (8 MB, held in
+    L2), values all one -- the hardware rate that bounds any CSR product on
+    random columns.  Returns gathers per second and per SM per clock (at the
+    clock sampled meanwhile)."""
+    import torch
+
+    import paper_1409_0669_gb300 as lak
+    from paper_1409_0669_gb300.timing import launch_time_us
+    g = torch.Generator(device=device).manual_seed(77)
+    idx = torch.randint(0, n_y, (n_gather,), generator=g, device=device, dtype=torch.int32)
+    vals = torch.ones(n_gather, device=device)
+    y = torch.rand(n_y, generator=g, device=device)
+    out = torch.empty(1, device=device)
+    ws = torch.zeros(lak.vec_dot_sparse_workspace(n_gather, "f32"), dtype=torch.uint8,
+                     device=device)
+    sampler = ClockSampler(device.index)
+    sampler.start()
+    time.sleep(0.1)
+    lak.vec_dot_sparse(vals, idx, y, out=out, workspace=ws)
+    us = launch_time_us(lambda: lak.vec_dot_sparse(vals, idx, y, out=out, workspace=ws), reps)
+    clocks = sampler.stop()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    rate = n_gather / (us * 1e-6)
+    mhz = clocks.get("sm_mhz")
+    del idx, vals, y, ws
+    return {"gathers_per_s": rate, "us": us, "gathers": n_gather, "y_entries": n_y,
+            "per_sm_per_clk": rate / (sms * mhz * 1e6) if mhz else None, "sm_mhz": mhz}
 
 
 def run_small(device, reps=200):

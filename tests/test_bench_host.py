@@ -195,7 +195,9 @@ def test_headline_is_compact_and_complete():
                           launches=124, roofline=roof, per_kernel=per, e2e=e2e, cpu=cpu,
                           clocks=clocks, detail_path="/some/where/bench_detail.json",
                           probe={"tflops": 1.2345678901, "sm_mhz": 2070.0,
-                                 "fma_per_sm_per_clk": 1.9612345, "ms_per_launch": 40.1234})
+                                 "fma_per_sm_per_clk": 1.9612345, "ms_per_launch": 40.1234},
+                          gprobe={"gathers_per_s": 270.123456e9, "per_sm_per_clk": 0.8612345,
+                                  "us": 118.7654, "sm_mhz": 2070.0})
     text = json.dumps(line, separators=(",", ":"))
     assert len(text.encode()) <= bench.HEADLINE_MAX_BYTES, len(text)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
