@@ -781,6 +781,16 @@ def run_autograd(device, reps=20):
         ag.gemv(Ar, xr).backward(dy)
     rec("gemv_forward_backward_autograd", full, 3 * (m * n + m + n) * 4)
 
+    # the same forward and backward captured once as CUDA graphs (torch replays
+    # a forward graph and a backward graph; the kernels are the same launches)
+    gemv_graphed = torch.cuda.make_graphed_callables(ag.gemv, (Ar, xr))
+
+    def full_graphed():
+        Ar.grad = None
+        xr.grad = None
+        gemv_graphed(Ar, xr).backward(dy)
+    rec("gemv_forward_backward_graphed", full_graphed, 3 * (m * n + m + n) * 4)
+
     rp, ci, v = synth.laplacian_3d(64, "f32")
     mm = rp.numel() - 1
     nnz = v.numel()

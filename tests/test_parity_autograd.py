@@ -155,3 +155,32 @@ def test_dense_outer_row_loop(storage, m, n):
     torch.cuda.synchronize()
     ref = oracle.round_to(oracle.dense_outer(dy.cpu(), x.cpu()).ravel(), storage)
     assert np.array_equal(host(dA), ref)
+
+
+def test_gemv_forward_backward_replays_from_cuda_graphs():
+    """The differentiable GEMV captured as CUDA graphs (a forward graph and a
+    backward graph, torch.cuda.make_graphed_callables) gives the same output and
+    gradients, bit for bit, as the eager calls -- the same kernels in the same
+    launch shapes -- on several replays with new inputs."""
+    ag = AG()
+    m, n = 300, 517
+    A = synth.normal((m, n), 11, "f32").cuda().requires_grad_()
+    x = synth.uniform(n, 12, "f32").cuda().requires_grad_()
+    graphed = torch.cuda.make_graphed_callables(ag.gemv, (A, x))
+    for rep in range(3):
+        with torch.no_grad():
+            A.copy_(synth.normal((m, n), 20 + rep, "f32").cuda())
+            x.copy_(synth.uniform(n, 30 + rep, "f32").cuda())
+        dy = synth.uniform(m, 40 + rep, "f32").cuda()
+        A.grad = x.grad = None
+        y_g = graphed(A, x)
+        y_g.backward(dy)
+        gA, gx = A.grad.clone(), x.grad.clone()
+        A.grad = x.grad = None
+        y_e = ag.gemv(A, x)
+        y_e.backward(dy)
+        torch.cuda.synchronize()
+        assert torch.equal(y_g, y_e)
+        assert torch.equal(gA, A.grad) and torch.equal(gx, x.grad)
+        assert_normwise(host(y_g.detach()), oracle.gemv(A.detach().cpu(), x.detach().cpu(),
+                                                       m, n, n), "f32")
