@@ -781,15 +781,23 @@ def run_autograd(device, reps=20):
         ag.gemv(Ar, xr).backward(dy)
     rec("gemv_forward_backward_autograd", full, 3 * (m * n + m + n) * 4)
 
-    # the same forward and backward captured once as CUDA graphs (torch replays
-    # a forward graph and a backward graph; the kernels are the same launches)
-    gemv_graphed = torch.cuda.make_graphed_callables(ag.gemv, (Ar, xr))
-
-    def full_graphed():
-        Ar.grad = None
-        xr.grad = None
-        gemv_graphed(Ar, xr).backward(dy)
-    rec("gemv_forward_backward_graphed", full_graphed, 3 * (m * n + m + n) * 4)
+    # the whole forward + backward step captured once into one CUDA graph (the
+    # gradients land in the .grad tensors allocated during capture) and replayed:
+    # the same kernels with no per-call host work
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            full()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    Ar.grad = None
+    xr.grad = None
+    step_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(step_graph):
+        ag.gemv(Ar, xr).backward(dy)
+    rec("gemv_forward_backward_one_graph", step_graph.replay, 3 * (m * n + m + n) * 4)
+    del step_graph
 
     rp, ci, v = synth.laplacian_3d(64, "f32")
     mm = rp.numel() - 1

@@ -158,29 +158,44 @@ def test_dense_outer_row_loop(storage, m, n):
 
 
 def test_gemv_forward_backward_replays_from_cuda_graphs():
-    """The differentiable GEMV captured as CUDA graphs (a forward graph and a
-    backward graph, torch.cuda.make_graphed_callables) gives the same output and
-    gradients, bit for bit, as the eager calls -- the same kernels in the same
-    launch shapes -- on several replays with new inputs."""
+    """The differentiable GEMV's whole forward + backward step captured once into
+    a CUDA graph (gradients written into the .grad tensors allocated during
+    capture) gives, on every replay with new inputs, the same output and
+    gradients bit for bit as the eager calls -- the same kernels in the same
+    launch shapes."""
     ag = AG()
     m, n = 300, 517
     A = synth.normal((m, n), 11, "f32").cuda().requires_grad_()
     x = synth.uniform(n, 12, "f32").cuda().requires_grad_()
-    graphed = torch.cuda.make_graphed_callables(ag.gemv, (A, x))
+    dy = synth.uniform(m, 13, "f32").cuda()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            A.grad = x.grad = None
+            ag.gemv(A, x).backward(dy)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    A.grad = x.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y_static = ag.gemv(A, x)
+        y_static.backward(dy)
+    gA_static, gx_static = A.grad, x.grad
     for rep in range(3):
         with torch.no_grad():
             A.copy_(synth.normal((m, n), 20 + rep, "f32").cuda())
             x.copy_(synth.uniform(n, 30 + rep, "f32").cuda())
-        dy = synth.uniform(m, 40 + rep, "f32").cuda()
-        A.grad = x.grad = None
-        y_g = graphed(A, x)
-        y_g.backward(dy)
-        gA, gx = A.grad.clone(), x.grad.clone()
+            dy.copy_(synth.uniform(m, 40 + rep, "f32").cuda())
+        g.replay()
+        torch.cuda.synchronize()
+        y_g, gA, gx = y_static.detach().clone(), gA_static.clone(), gx_static.clone()
         A.grad = x.grad = None
         y_e = ag.gemv(A, x)
         y_e.backward(dy)
         torch.cuda.synchronize()
-        assert torch.equal(y_g, y_e)
+        assert torch.equal(y_g, y_e.detach())
         assert torch.equal(gA, A.grad) and torch.equal(gx, x.grad)
-        assert_normwise(host(y_g.detach()), oracle.gemv(A.detach().cpu(), x.detach().cpu(),
-                                                       m, n, n), "f32")
+        assert_normwise(host(y_g), oracle.gemv(A.detach().cpu(), x.detach().cpu(), m, n, n),
+                        "f32")
+        A.grad, x.grad = gA_static, gx_static      # the graph writes into these
