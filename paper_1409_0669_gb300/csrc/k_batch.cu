@@ -57,9 +57,10 @@ struct GemvItem {
 
 // Rows of lane groups of 4+ lanes are taken R at a time by one group: rows
 // r, r + P, ..., r + (R-1) P, which share their alignment to the access width,
-// so one x pack serves R rows and one reduction closes R sums.
+// so one x pack serves R rows and one reduction closes R sums.  Such groups
+// only occur with packs of at most 32 bytes, for which R = 4.
 __host__ __device__ constexpr int gemv_rows_per_group(int access_bytes) {
-    return access_bytes <= 16 ? 4 : 2;
+    return access_bytes <= 32 ? 4 : 2;
 }
 struct CsrItem {
     lak_csr_desc d;
@@ -237,7 +238,11 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // modulo the access width (P = 1 when lda * element size is a multiple of it),
 // so all R rows share one scalar head and one aligned body.  Measured on the
 // 4096-instance FP32 mix: 2.47 ms (6.05 TB/s) against 3.62 ms for one row per
-// lane group; FP64 7.8 against 9.0 ms, BF16 2.34 against 2.98 ms.
+// lane group; FP64 7.8 against 9.0 ms, BF16 2.34 against 2.98 ms.  At 32-byte
+// packs the body is not unrolled: four rows already keep four 32-byte loads in
+// flight per lane, and a second copy of them does not fit the 64 registers
+// (FP64 7.13 against 7.53 ms, BF16 1.81 against 2.12 ms for the same four rows
+// unrolled twice; 16-byte packs keep the unrolled body, 2.40 against 3.93 ms).
 
 // Sum of R per-lane values over each aligned group of G lanes (G a power of two,
 // 4..32) by halving exchanges: afterwards lane lg of a group holds the total of
@@ -306,7 +311,8 @@ __device__ __forceinline__ void gemv_group_rows(const GemvItem &it, int64_t r0, 
         const int64_t nch = nb / V;
         const T *xb = x + h;
         const bool xal = ((uintptr_t)xb % W) == 0;
-#pragma unroll 2
+        constexpr int kUnroll = W <= 16 ? 2 : 1;
+#pragma unroll kUnroll
         for (int64_t c = lg; c < nch; c += G) {
             Pack<T, V> px;
             if (xal) {

@@ -55,9 +55,9 @@ def test_gemv_rows_per_unit_and_spmv_units(nat):
     g = [nat.GemvDesc(256, 512, 768, m, n, max(n, 1))
          for m, n in ((2000, 64), (40, 4096), (3, 100000), (0, 5), (7, 0))]
     info, offs, _ = plan(nat, "gemv_row", "f32", g, cfg)
-    # rows per unit: 1024 -> 2 units; 16 -> 3 units; 1, rounded up to the 2 rows a warp
-    # takes at once for long rows with 32-byte accesses -> 2 units; none; n = 0: all 7 -> 1
-    assert list(offs) == [0, 2, 5, 7, 7, 8]
+    # rows per unit: 1024 -> 2 units; 16 -> 3 units; 1, rounded up to the 4 rows a lane
+    # group takes at once -> 1 unit; none; n = 0: all 7 -> 1
+    assert list(offs) == [0, 2, 5, 6, 6, 7]
     # CSR: one block's rows (64) per unit
     c = [nat.CsrDesc(256, 512, 768, 1024, 1280, m, m, 5 * m) for m in (1, 64, 65, 1000)]
     info, offs, _ = plan(nat, "spmv", "f32", c, nat.LakCfg(64, 0, 4, 0))
@@ -136,9 +136,9 @@ def test_gemv_long_rows_period_and_units(nat):
         (1024, 1024, 4, 32, 1, 4),      # 4096 B: P = 1
         (300, 301, 4, 16, 4, 4),        # 16 lanes per row
         (100, 101, 4, 8, 4, 4),         # 8 lanes per row
-        (2049, 2049, 8, 32, 8, 2),      # 32-byte accesses: P = 8, R = 2
-        (2050, 2052, 8, 32, 2, 2),      # 8208 B rows: P = 2
-        (300, 300, 8, 8, 2, 2),         # 8 lanes per row at 32 bytes: 1200 B rows, P = 2
+        (2049, 2049, 8, 32, 8, 4),      # 32-byte accesses: P = 8
+        (2050, 2052, 8, 32, 2, 4),      # 8208 B rows: P = 2
+        (300, 300, 8, 8, 2, 4),         # 8 lanes per row at 32 bytes: 1200 B rows, P = 2
     ]
     for n, lda, vec, G, P, R in cases:
         m = 333
@@ -149,11 +149,11 @@ def test_gemv_long_rows_period_and_units(nat):
         assert group == G and period == P, (n, lda, vec, group, period)
         assert rpu % (R * P) == 0 and rpu >= min(65536 // n, m)
         assert list(offs) == [0, -(-m // rpu)]
-    # 4 lanes per row (short rows at 32-byte accesses) take 2 rows at a time too
+    # 4 lanes per row (short rows at 32-byte accesses) take 4 rows at a time too
     info, offs, raw = plan(nat, "gemv_row", "f32", [nat.GemvDesc(256, 512, 768, 50, 100, 101)],
                            nat.LakCfg(128, 0, 8, 0))
     rpu, _, group, period = struct.unpack_from("<qiii", raw, (64 + 16 + 15) // 16 * 16 + 48)
-    assert group == 4 and period == 8 and rpu % 16 == 0
+    assert group == 4 and period == 8 and rpu % 32 == 0
     # FP64 at 16 elements per access (two 32-byte loads): 1-2 lanes per short row,
     # one row at a time
     info, offs, raw = plan(nat, "gemv_row", "f64", [nat.GemvDesc(256, 512, 768, 50, 100, 101)],
