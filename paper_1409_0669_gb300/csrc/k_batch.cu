@@ -241,8 +241,9 @@ dot_batch_kernel(const BatchHead *__restrict__ head, const int64_t *__restrict__
 // lane group; FP64 7.8 against 9.0 ms, BF16 2.34 against 2.98 ms.  At 32-byte
 // packs the body is not unrolled: four rows already keep four 32-byte loads in
 // flight per lane, and a second copy of them does not fit the 64 registers
-// (FP64 7.13 against 7.53 ms, BF16 1.81 against 2.12 ms for the same four rows
-// unrolled twice; 16-byte packs keep the unrolled body, 2.40 against 3.93 ms).
+// (FP64 7.13 ms against 7.40 for the same four rows unrolled twice and 7.53 for
+// two rows unrolled twice; BF16 1.81 against 1.92 and 2.12 ms).  16-byte packs
+// keep the unrolled body (FP32 2.40 against 3.93 ms).
 
 // Sum of R per-lane values over each aligned group of G lanes (G a power of two,
 // 4..32) by halving exchanges: afterwards lane lg of a group holds the total of
