@@ -31,7 +31,7 @@ __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
     int64_t head = mis ? (int64_t)(W / ES) - mis : 0;
     if (head > n) head = n;
     for (int64_t j = lg; j < head; j += G)
-        acc[0] = fma_acc(widen(Ar[j]), widen(ld_cached(x + j)), acc[0]);
+        acc[0] = fma_wide(Ar[j], ld_cached(x + j), acc[0]);
     const T *Ab = Ar + head;
     const T *xb = x + head;
     const int64_t nb = n - head;
@@ -45,7 +45,7 @@ __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 Ac &a = gemv_one_chain<T> ? acc[0] : acc[v];
-                a = fma_acc(widen(pa.e[v]), widen(px.e[v]), a);
+                a = fma_wide(pa.e[v], px.e[v], a);
             }
         }
     } else {
@@ -56,12 +56,12 @@ __device__ __forceinline__ void row_group_dot(typename Acc<T>::type (&acc)[V],
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 Ac &a = gemv_one_chain<T> ? acc[0] : acc[v];
-                a = fma_acc(widen(pa.e[v]), widen(ld_cached(xb + c * V + v)), a);
+                a = fma_wide(pa.e[v], ld_cached(xb + c * V + v), a);
             }
         }
     }
     for (int64_t j = nch * V + lg; j < nb; j += G)
-        acc[0] = fma_acc(widen(Ab[j]), widen(ld_cached(xb + j)), acc[0]);
+        acc[0] = fma_wide(Ab[j], ld_cached(xb + j), acc[0]);
 }
 
 }  // namespace lak

@@ -303,10 +303,10 @@ __device__ __forceinline__ void gemv_group_rows(const GemvItem &it, int64_t r0, 
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[j] = Ac(0);
         for (int64_t k = lg; k < h; k += G) {
-            const Ac xv = widen(ld_cached(x + k));
+            const T xv = ld_cached(x + k);
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                if (ok[j]) acc[j] = fma_acc(widen(a[j][k]), xv, acc[j]);
+                if (ok[j]) acc[j] = fma_wide(a[j][k], xv, acc[j]);
         }
         const int64_t nb = n - h;
         const int64_t nch = nb / V;
@@ -328,14 +328,14 @@ __device__ __forceinline__ void gemv_group_rows(const GemvItem &it, int64_t r0, 
                 Pack<T, V> pa;
                 load_pack<T, V, STREAM>(pa, a[j] + h + c * V);
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[j] = fma_acc(widen(pa.e[v]), widen(px.e[v]), acc[j]);
+                for (int v = 0; v < V; ++v) acc[j] = fma_wide(pa.e[v], px.e[v], acc[j]);
             }
         }
         for (int64_t k = h + nch * V + lg; k < n; k += G) {
-            const Ac xv = widen(ld_cached(x + k));
+            const T xv = ld_cached(x + k);
 #pragma unroll
             for (int j = 0; j < R; ++j)
-                if (ok[j]) acc[j] = fma_acc(widen(a[j][k]), xv, acc[j]);
+                if (ok[j]) acc[j] = fma_wide(a[j][k], xv, acc[j]);
         }
         const Ac s = group_sum_rows<Ac, R>(acc, lg, G);
         const int per = G / R;                                  // lanes holding one row's sum

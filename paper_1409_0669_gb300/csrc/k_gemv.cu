@@ -135,16 +135,16 @@ gemv_col_kernel(T *__restrict__ y, const T *__restrict__ A, const T *__restrict_
         for (int64_t j = c0 + warp; j < c1; j += nwarps) {
             Pack<T, V> pa;
             load_pack<T, V, STREAM>(pa, A + j * lda + r0);
-            const Ac xj = widen(ld_cached(x + j));
+            const T xj = ld_cached(x + j);
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fma_acc(widen(pa.e[v]), xj, acc[v]);
+            for (int v = 0; v < V; ++v) acc[v] = fma_wide(pa.e[v], xj, acc[v]);
         }
     } else if (r0 < m) {
         for (int64_t j = c0 + warp; j < c1; j += nwarps) {
-            const Ac xj = widen(ld_cached(x + j));
+            const T xj = ld_cached(x + j);
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                if (r0 + v < m) acc[v] = fma_acc(widen(A[j * lda + r0 + v]), xj, acc[v]);
+                if (r0 + v < m) acc[v] = fma_wide(A[j * lda + r0 + v], xj, acc[v]);
         }
     }
 #pragma unroll

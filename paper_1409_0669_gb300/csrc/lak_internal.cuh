@@ -171,6 +171,29 @@ template <> __device__ __forceinline__ __half narrow<__half>(float v) { return _
 __device__ __forceinline__ float fma_acc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_acc(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// a * b + c for two stored values and the accumulator, rounded once.  FP32 and
+// FP64 storage: one FMA.  16-bit storage: one mixed-precision FMA (16-bit
+// factors, FP32 addend and result) -- widening a 16-bit value to FP32 is exact,
+// so this is the same FMA on the same values as widening both factors first
+// (one PTX instruction instead of two conversions and an FMA; the results are
+// bit-identical).  The dense products use it: BF16 / FP16 GEMV 2-4 % faster
+// (row-major, column-major, batched).  The streaming inner products keep the
+// widened form, which measured 11 % faster there.
+__device__ __forceinline__ float fma_wide(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_wide(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_wide(__nv_bfloat16 a, __nv_bfloat16 b, float c) {
+    float d;
+    asm("fma.rn.f32.bf16 %0, %1, %2, %3;"
+        : "=f"(d) : "h"(__bfloat16_as_ushort(a)), "h"(__bfloat16_as_ushort(b)), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fma_wide(__half a, __half b, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;"
+        : "=f"(d) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(c));
+    return d;
+}
+
 // ---------------------------------------------------------------------------
 // Device side: wide loads and stores
 // ---------------------------------------------------------------------------
