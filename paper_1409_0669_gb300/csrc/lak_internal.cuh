@@ -69,7 +69,8 @@ inline int access_bytes(int vec, int es) {
 // next grid is scheduled once every block of this one has started, so its
 // launch and block set-up overlap this grid's tail instead of following it).
 // No kernel touches global memory before the wait, so the stream's ordering is
-// unchanged; launch_k launches with the attribute unless LAK_PDL=0.
+// unchanged; launch_k launches with the attribute unless LAK_PDL=0.  (The
+// batched GEMV only waits; it lets its dependents launch when it completes.)
 #define LAK_PDL_ENTRY()                                              \
     do {                                                             \
         asm volatile("griddepcontrol.wait;" ::: "memory");           \
