@@ -557,8 +557,9 @@ LAK_API lak_status lak_batch_run(const lak_batch_info *info, const void *dev_tab
  * given no cfg (the batched form of Sec. 2's tuning parameters, chosen by this
  * library's autotuner over the batching workload).  cfg = NULL or block 0
  * removes the entry (back to the built-in shape).  block: 32..512 in steps of
- * 32 (batched GEMV: at most 128); grid >= 0 (0 = as many blocks as fit on the
- * device at once); vec 0 (the built-in width) or 1, 2, 4, 8, 16 (CSR uses 4 or
+ * 32 (batched GEMV: at most 128); grid >= 0 (0 = the SM count times the blocks
+ * of `block` threads an SM holds by thread count, 2048 / block; capped at the
+ * batch's work units); vec 0 (the built-in width) or 1, 2, 4, 8, 16 (CSR uses 4 or
  * 8 entries per lane and clamps to that range).  Host only; process-wide;
  * plans made earlier keep their configuration.
  */

@@ -290,7 +290,7 @@ def study_table(reports: List[Dict]) -> str:
 # ---- batched launches -------------------------------------------------------------
 
 BATCH_OPS = ("axpy", "dot", "gemv_row", "spmv")
-BATCH_GRID_PER_SM = (0, 1, 2, 4, 8, 16)          # 0 = as many blocks as fit at once
+BATCH_GRID_PER_SM = (0, 1, 2, 4, 8, 16)          # 0 = SMs x (2048 / block threads)
 
 
 def batch_space(op: str, sms: int) -> List[LakCfg]:
