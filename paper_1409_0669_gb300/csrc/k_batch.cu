@@ -8,11 +8,14 @@
 // instance, and per-instance items (the caller's descriptor plus the launch
 // details the plan chose).  lak_batch_run launches one persistent grid over
 // all units; a block maps its unit to an instance with a binary search over
-// the prefix (a few L1-resident loads) and runs the same inner loops as the
-// single-instance kernels (dense rows with a lane group per row sized from the
-// row length; CSR rows with the warp-segmented body).  Batched dot products finish per instance with the
-// last-arriving-unit combine (an arrival counter per instance in the workspace
-// counter area), in unit order, so results are deterministic.
+// the prefix (a few L1-resident loads) and runs the inner loops of the
+// single-instance kernels, except for dense rows: a lane group per row sized
+// from the row length takes four rows at a time, and at 16-byte accesses the
+// rows reach the lanes through a shared-memory ring of asynchronous copies
+// (gemv_group_rows); CSR rows take the warp-segmented body.  Batched dot
+// products finish per instance with the last-arriving-unit combine (an arrival
+// counter per instance in the workspace counter area), in unit order, so
+// results are deterministic.
 #include <cstddef>
 
 #include "gemv_row.cuh"
