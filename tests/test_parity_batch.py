@@ -391,3 +391,37 @@ def test_gemv_batch_adversarial_shapes(storage, vec):
             assert_reduced_sum(host(y), ref, abs_ref, np.full(m, n), storage, what)
         else:
             assert_normwise_scaled(host(y), ref, abs_ref, storage, what)
+
+
+@pytest.mark.parametrize("vec", [4, 8, 16])
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+def test_gemv_batch_misaligned_x(storage, vec):
+    """Right-hand sides that start 0..7 elements past an aligned address (views
+    of one buffer), against matrices whose rows start at every offset: the x
+    reads of the shared-memory ring path and of the register path, aligned and
+    element by element, every instance against the oracle."""
+    dt = synth.torch_dtype(storage)
+    shapes = [(m, n) for m in (1, 4, 5, 9, 33) for n in (7, 16, 31, 64, 100, 257, 1000)]
+    xtotal = sum(n + 8 for _, n in shapes)
+    xflat = synth.uniform(xtotal, 800, storage).cuda()
+    As, xs, ys = [], [], []
+    xo = 0
+    for i, (m, n) in enumerate(shapes):
+        lda = n + i % 3
+        As.append(synth.normal((m * lda,), 900 + i, storage).cuda().view(m, lda)[:, :n])
+        off = i % 8
+        xs.append(xflat[xo + off:xo + off + n])
+        xo += n + 8
+        ys.append(torch.full((m,), float("nan"), dtype=dt, device="cuda"))
+    b = B().gemv_batch(As, xs, ys, cfg=(128, 0, vec, 0))
+    b.run()
+    torch.cuda.synchronize()
+    for i, (A, x, y, (m, n)) in enumerate(zip(As, xs, ys, shapes)):
+        sub = A.contiguous().reshape(-1).cpu()
+        ref = oracle.gemv(sub, x.cpu(), m, n, n, "row")
+        abs_ref = oracle.gemv(np.abs(oracle.widen(sub)), np.abs(host(x)), m, n, n, "row")
+        what = f"instance {i} {m}x{n} x offset {i % 8} vec {vec}"
+        if storage in ("bf16", "f16"):
+            assert_reduced_sum(host(y), ref, abs_ref, np.full(m, n), storage, what)
+        else:
+            assert_normwise_scaled(host(y), ref, abs_ref, storage, what)
