@@ -214,6 +214,55 @@ def test_batch_replays_from_cuda_graph():
     assert torch.equal(out, first)
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_families_back_to_back_in_one_graph(storage):
+    """The dot, GEMV and CSR batches captured back to back in one graph (each
+    kernel waits for the one before; the GEMV lets the next launch only when it
+    has finished): outputs identical to the same batches run one at a time,
+    over several replays that each start from overwritten outputs."""
+    dt = synth.torch_dtype(storage)
+    ns = sizes(40, 100, 20_000, 9)
+    xs = [synth.uniform(n, 300 + i, storage).cuda() for i, n in enumerate(ns)]
+    zs = [synth.uniform(n, 400 + i, storage).cuda() for i, n in enumerate(ns)]
+    dots = torch.zeros(len(ns), device="cuda")
+    shapes = list(zip(sizes(30, 1, 600, 10, extra=(1, 4)), sizes(30, 1, 900, 11, extra=(7, 64))))
+    As = [synth.normal((m, n), 500 + i, storage).cuda() for i, (m, n) in enumerate(shapes)]
+    gx = [synth.uniform(n, 600 + i, storage).cuda() for i, (m, n) in enumerate(shapes)]
+    gy = [torch.zeros(m, dtype=dt, device="cuda") for m, _ in shapes]
+    csrs, cx, cy = [], [], []
+    for i, m in enumerate(sizes(12, 500, 20_000, 12)):
+        rp, ci, v = synth.random_csr(m, m, 700 + i, storage, min_len=5, max_len=64)
+        csrs.append((rp.cuda(), ci.cuda(), v.cuda(), m))
+        cx.append(synth.uniform(m, 800 + i, storage).cuda())
+        cy.append(torch.zeros(m, dtype=dt, device="cuda"))
+    bd = B().dot_batch(xs, zs, [dots[i:i + 1] for i in range(len(ns))])
+    bg = B().gemv_batch(As, gx, gy)
+    bs = B().spmv_batch(csrs, cx, cy)
+    outs = [dots] + gy + cy
+    for b in (bd, bg, bs):
+        b.run()
+    torch.cuda.synchronize()
+    alone = [o.clone() for o in outs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for b in (bd, bg, bs):
+            b.run(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for b in (bd, bg, bs):
+            b.run()
+    for _ in range(3):
+        for o in outs:
+            o.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for o, a in zip(outs, alone):
+            assert torch.equal(o, a)
+
+
 def test_spmv_batch_ticket_counters_reset_between_runs():
     """The CSR batch's warps take their rows from ticket counters in the
     workspace, which the last warp resets: every run, direct or replayed from a
