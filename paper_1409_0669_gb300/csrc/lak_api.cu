@@ -123,34 +123,46 @@ int bucket_of(int64_t bytes) {
 //   grid_per_sm  vector ops: cap of the automatic grid, in blocks per SM;
 //                dense_gemv / csr_spmv: the grid itself in blocks per SM
 //                (0 = the op's automatic grid)
-//   vec          elements per access for the row's type (FP32 row: BF16/FP16
-//                take the same bytes per access; csr_spmv: loads per lane)
+//   vec          elements per access of the row's storage type (csr_spmv:
+//                loads per lane)
 //   inc          LAK_INC_GLOBAL / LAK_INC_LOCAL
 struct DefaultCfg {
     int block, grid_per_sm, vec, inc;
 };
 
 constexpr int G_ = LAK_INC_GLOBAL, L_ = LAK_INC_LOCAL;
-// [op][0 = FP32 (and BF16/FP16), 1 = FP64][bucket]
-constexpr DefaultCfg kDefaults[LAK_OP_COUNT][2][LAK_SIZE_BUCKETS] = {
+// [op][0 = FP32, 1 = FP64, 2 = 16-bit storage (BF16 / FP16)][bucket].  Each
+// 16-bit entry is the better of two candidates timed side by side on BF16 at the
+// bucket's sweep sizes (best worst-case ratio): the FP32 entry at the same bytes
+// per access, and the autotuner's own BF16 choice.  Copy, the CSR kernel and
+// the smallest column-major GEMV bucket keep the FP32 entries; the update, the
+// inner product and the GEMVs gain up to 1.2-1.4x at some sizes from the
+// BF16-tuned ones.
+constexpr DefaultCfg kDefaults[LAK_OP_COUNT][3][LAK_SIZE_BUCKETS] = {
     // copy
     {{{128, 32, 8, G_}, {128, 8, 16, L_}, {256, 32, 8, G_}, {512, 32, 16, G_}},
-     {{512, 4, 4, G_}, {64, 32, 8, G_}, {256, 32, 4, G_}, {512, 32, 8, G_}}},
+     {{512, 4, 4, G_}, {64, 32, 8, G_}, {256, 32, 4, G_}, {512, 32, 8, G_}},
+     {{128, 32, 16, G_}, {128, 8, 16, L_}, {256, 32, 16, G_}, {512, 32, 16, G_}}},
     // axpy (and axpby, the fused update + norm)
     {{{256, 32, 8, G_}, {128, 32, 4, G_}, {128, 32, 8, G_}, {512, 32, 16, G_}},
-     {{256, 16, 2, G_}, {256, 8, 2, G_}, {128, 32, 4, G_}, {512, 32, 8, G_}}},
+     {{256, 16, 2, G_}, {256, 8, 2, G_}, {128, 32, 4, G_}, {512, 32, 8, G_}},
+     {{256, 4, 4, G_}, {256, 0, 8, G_}, {128, 32, 16, G_}, {512, 32, 16, G_}}},
     // dot
     {{{256, 8, 8, G_}, {512, 4, 4, G_}, {512, 1, 16, G_}, {512, 2, 8, G_}},
-     {{256, 1, 2, G_}, {512, 1, 4, G_}, {512, 2, 1, G_}, {256, 4, 4, G_}}},
+     {{256, 1, 2, G_}, {512, 1, 4, G_}, {512, 2, 1, G_}, {256, 4, 4, G_}},
+     {{256, 0, 16, G_}, {256, 4, 8, G_}, {512, 2, 8, G_}, {512, 2, 16, G_}}},
     // row-major GEMV
     {{{256, 0, 2, G_}, {128, 8, 8, G_}, {32, 32, 8, G_}, {64, 0, 8, G_}},
-     {{128, 8, 4, G_}, {32, 16, 8, G_}, {32, 0, 2, G_}, {32, 0, 8, G_}}},
+     {{128, 8, 4, G_}, {32, 16, 8, G_}, {32, 0, 2, G_}, {32, 0, 8, G_}},
+     {{128, 0, 2, G_}, {128, 8, 8, G_}, {32, 32, 8, G_}, {64, 0, 8, G_}}},
     // column-major GEMV
     {{{512, 1, 4, L_}, {512, 0, 8, G_}, {512, 2, 8, L_}, {128, 0, 4, G_}},
-     {{512, 4, 2, G_}, {512, 2, 4, G_}, {128, 8, 2, L_}, {512, 16, 2, L_}}},
+     {{512, 4, 2, G_}, {512, 2, 4, G_}, {128, 8, 2, L_}, {512, 16, 2, L_}},
+     {{512, 1, 8, L_}, {512, 4, 8, G_}, {512, 4, 8, L_}, {256, 8, 8, L_}}},
     // CSR SpMV, group-per-row kernel (short and long rows)
     {{{512, 2, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}},
-     {{256, 0, 4, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}}},
+     {{256, 0, 4, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}, {64, 16, 8, G_}},
+     {{512, 2, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}, {128, 16, 4, G_}}},
 };
 
 // CSR SpMV, warp-segmented kernel (mean row length 13..64): tuned on the
@@ -165,12 +177,9 @@ constexpr DefaultCfg kSpmvSegDefaults[2][LAK_SIZE_BUCKETS] = {
 
 bool is_vector_op(lak_op op) { return op == LAK_OP_COPY || op == LAK_OP_AXPY || op == LAK_OP_DOT; }
 
-DefaultCfg default_row(lak_op op, lak_dtype dt, int bucket) {
-    DefaultCfg d = kDefaults[op][dt == LAK_F64 ? 1 : 0][bucket];
-    if ((dt == LAK_BF16 || dt == LAK_F16) && op != LAK_OP_SPMV)
-        d.vec = d.vec * 2 > 16 ? 16 : d.vec * 2;      // same bytes per access as FP32
-    return d;
-}
+int storage_row(lak_dtype dt) { return dt == LAK_F64 ? 1 : (dt == LAK_BF16 || dt == LAK_F16) ? 2 : 0; }
+
+DefaultCfg default_row(lak_op op, lak_dtype dt, int bucket) { return kDefaults[op][storage_row(dt)][bucket]; }
 
 // Fallback launch shapes of the batched persistent kernels (lak_batch_run), used
 // only where no autotuned entry is installed (lak_set_batch_default_cfg; the

@@ -31,9 +31,17 @@ def test_resolve_follows_bucket():
     # column-major FP64 GEMV 2048^2 (33.6 MB, bucket 1): explicit grid from the table
     g = m.resolve_cfg("gemv_col", "f64", 2048, 2048)
     assert g.block == 512 and g.vec == 4 and g.grid == 2 * sms()
-    # BF16 takes the FP32 row's bytes per access: copy bucket 3 = 64 B -> 16 x 2 B... capped at 16
-    b = m.resolve_cfg("copy", "bf16", 10 ** 9, 10 ** 9)
-    assert b.vec == 16
+    # 16-bit storage has its own rows: the dot of 1e6 BF16 values (4 MB, bucket
+    # 0) takes the BF16-tuned entry (256 threads, 16 per access, automatic grid),
+    # the copy keeps the FP32 entry at the same bytes per access (128 threads,
+    # 8 x 4 B -> 16 x 2 B); FP16 takes the same rows
+    for st in ("bf16", "f16"):
+        d = m.resolve_cfg("dot", st, 10 ** 6, 10 ** 6)
+        assert (d.block, d.vec) == (256, 16)
+        b = m.resolve_cfg("copy", st, 10 ** 6, 10 ** 6)
+        assert (b.block, b.vec) == (128, 16)
+    g = m.resolve_cfg("gemv_row", "bf16", 1024, 1024)
+    assert (g.block, g.vec) == (128, 2)
 
 
 def test_bucket_override_stays_in_its_bucket():
