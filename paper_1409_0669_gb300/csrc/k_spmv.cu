@@ -93,7 +93,7 @@ spmv_kernel(T *__restrict__ y, const int32_t *__restrict__ rp, const int32_t *__
 
 // Warp-segmented variant: the 32-row block body lives in spmv_seg.cuh (shared
 // with the batched kernel); this kernel hands each warp its 32-row blocks.
-template <typename T, int U, bool VLOAD>
+template <typename T, int U, bool VLOAD, int WMAX = 16>
 __global__ void __launch_bounds__(512)
 spmv_seg_kernel(T *__restrict__ y, const int32_t *__restrict__ rp,
                 const int32_t *__restrict__ ci, const T *__restrict__ vals,
@@ -105,15 +105,16 @@ spmv_seg_kernel(T *__restrict__ y, const int32_t *__restrict__ rp,
     uint32_t *rs_w;
     Ac *racc_w;
     if constexpr (sizeof(Ac) == 8) {
-        __shared__ uint32_t rs_all[16][33];
-        __shared__ Ac racc_all[16][32];
+        __shared__ uint32_t rs_all[WMAX][33];
+        __shared__ Ac racc_all[WMAX][32];
         rs_w = rs_all[warp];
         racc_w = racc_all[warp];
     } else {
         // sized to the block's warps (the launch passes the bytes), which leaves
         // more of the unified L1 to the x gathers: FP32 power-law 142.0 -> 140.0-
-        // 141.0 us.  FP64 keeps the static arrays: the same change there cost two
-        // registers and 2 % (178.9 -> 182.9 us).
+        // 141.0 us.  FP64 keeps static arrays, sized for WMAX warps (2 for its
+        // 64-thread default blocks: 178.8 -> 176.8 us); the dynamic form cost it
+        // two registers and 2 % (178.9 -> 182.9 us).
         extern __shared__ __align__(16) unsigned char seg_smem[];
         racc_w = reinterpret_cast<Ac *>(seg_smem) + (size_t)warp * 32;
         rs_w = reinterpret_cast<uint32_t *>(seg_smem + (size_t)wpb * 32 * sizeof(Ac)) + (size_t)warp * 33;
@@ -145,7 +146,10 @@ lak_status spmv_seg_launch(T *yp, const int32_t *rp, const int32_t *ci, const T 
     const size_t smem = sizeof(Ac) == 8 ? 0 : (size_t)(L.block / 32) * (32 * sizeof(Ac) + 33 * 4);
     if constexpr (U % 4 == 0) {
         if (vload) {
-            launch_k(spmv_seg_kernel<T, U, true>, L.grid, L.block, smem, s, yp, rp, ci, vp, xp, m, L.inc);
+            if (sizeof(Ac) == 8 && L.block <= 64)
+                launch_k(spmv_seg_kernel<T, U, true, 2>, L.grid, L.block, smem, s, yp, rp, ci, vp, xp, m, L.inc);
+            else
+                launch_k(spmv_seg_kernel<T, U, true>, L.grid, L.block, smem, s, yp, rp, ci, vp, xp, m, L.inc);
             return check_launch("csr_spmv (warp-segmented)");
         }
     }
