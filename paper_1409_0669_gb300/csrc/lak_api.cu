@@ -167,12 +167,16 @@ constexpr DefaultCfg kDefaults[LAK_OP_COUNT][3][LAK_SIZE_BUCKETS] = {
 
 // CSR SpMV, warp-segmented kernel (mean row length 13..64): tuned on the
 // power-law matrix (2M rows), where the group-per-row entries above lose 6 %
-// (FP32) and 4 % (FP64).  FP64 takes 4 entries per lane: at 54 registers a
+// (FP32) and 4 % (FP64).  FP64 takes 4 entries per lane: at 48-50 registers a
 // thread that leaves more warps resident than 8 entries (60 registers), and
-// the gathers, not the FP64 pipe, bound this kernel now (186 vs 195 us).
-constexpr DefaultCfg kSpmvSegDefaults[2][LAK_SIZE_BUCKETS] = {
-    {{128, 0, 4, G_}, {128, 0, 4, G_}, {128, 0, 4, G_}, {128, 0, 4, G_}},
+// the gathers, not the FP64 pipe, bound this kernel now (186 vs 195 us).  The
+// large buckets follow the re-ranking tuner's sweep on the current kernel
+// (FP32 64 threads: 139.3 against 140.5 us at 128; 16-bit 64 threads and 8
+// entries per lane: 129.4 against 132.9 us).  [0 = FP32, 1 = FP64, 2 = 16-bit]
+constexpr DefaultCfg kSpmvSegDefaults[3][LAK_SIZE_BUCKETS] = {
+    {{128, 0, 4, G_}, {128, 0, 4, G_}, {64, 0, 4, G_}, {64, 0, 4, G_}},
     {{64, 0, 4, G_}, {64, 0, 4, G_}, {64, 0, 4, G_}, {64, 0, 4, G_}},
+    {{128, 0, 4, G_}, {128, 0, 4, G_}, {64, 0, 8, G_}, {64, 0, 8, G_}},
 };
 
 bool is_vector_op(lak_op op) { return op == LAK_OP_COPY || op == LAK_OP_AXPY || op == LAK_OP_DOT; }
@@ -422,7 +426,7 @@ int64_t spmv_seg_max_mean() {
 // The built-in default for the warp-segmented SpMV kernel (an override set for
 // LAK_OP_SPMV applies to both SpMV kernels).
 lak_cfg seg_default(lak_dtype dt, int bucket) {
-    const DefaultCfg d = kSpmvSegDefaults[dt == LAK_F64 ? 1 : 0][bucket];
+    const DefaultCfg d = kSpmvSegDefaults[storage_row(dt)][bucket];
     lak_cfg c{d.block, 0, d.vec, d.inc};
     if (d.grid_per_sm > 0) {
         const DeviceInfo *di = device_info();
